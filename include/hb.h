@@ -1,0 +1,198 @@
+/*
+ * hb.h - C ABI of the GB300 Hadamard-Babich (HB) volume integrator.
+ *
+ * The library applies the discretised HB integrator of arXiv 2210.02698,
+ *     U = K^{v2v} I,   I_j = s(r_j) h^2            (Sec. 3.1, Eq. m_v2v)
+ * over the N_v = nx*ny cell centres of a regular 2D grid, with
+ *     K_ij = g(r_i, r_j) = v0 f0(w, tau) + v1 f1(w, tau)   (i != j, Eq. babich, N = 1)
+ *     f0 = i sqrt(pi)/2 H0(w tau),  f1 = -i sqrt(pi)/2 (2 tau / w) H1(w tau)   (Eq. termf)
+ * where tau^2, v0, v1 are Chebyshev-interpolated from tables at node pairs
+ * (Sec. 4.1, Eq. chebinterp) and K_ii is the cell-integrated self term of
+ * Appendix A (Eq. HankelIntegral2dlemma) divided by h^2.  The operator is
+ * applied densely (matrix free, FP64) or in HODBF / butterfly-compressed form
+ * (Sec. 4.2, Eq. butterfly_mat), in FP64 or with FP32 factors and split-BF16
+ * tensor-core products accumulated in FP32.
+ *
+ * Conventions shared by every entry point:
+ *  - Cells are in natural order: index = b*nx + a, a the x index (fastest),
+ *    centroid (x0 + (a+1/2) h, y0 + (b+1/2) h).
+ *  - Vectors s and u are caller-owned DEVICE buffers of complex128 values
+ *    (interleaved re, im), N_v x nrhs, column-major (one right-hand side
+ *    contiguous), natural order, unless a function says otherwise.
+ *  - hb_apply*(s -> u) computes u = K (h^2 s); hb_apply*_adjoint(u -> s)
+ *    computes its exact adjoint s = h^2 K^H u (conjugate transpose).
+ *  - Work is enqueued on the given cudaStream_t (passed as void*, NULL = the
+ *    legacy default stream) and is asynchronous unless stated.
+ *  - No exception crosses the ABI.  Every call returns an hb_status; the
+ *    message of the last failure is kept per handle (hb_last_error) or, for
+ *    calls without a handle, per thread (hb_last_error(NULL)).
+ *  - A handle is not thread-safe: use it from one host thread and one stream
+ *    at a time.  Calls on a handle serialise through its internal buffers.
+ *  - There is no CPU fallback: without a CUDA device every compute call
+ *    returns HB_ERR_CUDA.
+ */
+#ifndef HB_H_
+#define HB_H_
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hb_ctx* hb_handle;
+
+typedef enum {
+  HB_OK = 0,
+  HB_ERR_ARG = 1,          /* invalid argument (null pointer, size, option)   */
+  HB_ERR_CUDA = 2,         /* a CUDA runtime call or kernel failed            */
+  HB_ERR_OOM = 3,          /* device or host allocation failed                */
+  HB_ERR_TIMEOUT = 4,      /* a bounded device wait gave up                   */
+  HB_ERR_STATE = 5,        /* call not valid in the handle's state            */
+  HB_ERR_UNSUPPORTED = 6   /* valid request the library does not implement    */
+} hb_status;
+
+enum { HB_FP64 = 0, HB_MIXED_BF16X3 = 1 };
+
+/* Regular cell-centred 2D grid (Sec. 3.1): nx*ny cells of size h. */
+typedef struct {
+  int nx, ny;
+  double x0, y0, h;
+} hb_grid;
+
+/* Tabulated HB ingredients (Sec. 4.1).  All HOST pointers, copied by
+ * hb_create.  nodes_x / nodes_y: the n_I Chebyshev nodes per dimension in
+ * domain coordinates.  tau2, v0, v1: N_I x N_I row-major (N_I = n_I^2),
+ * row = observation node i, column = source node j, node index
+ * i = i2*n_I + i1 (x index fastest), i.e. F^c_ij = f(r^c_i, r^c_j) of
+ * Eq. chebinterp.  n_cells: n(r) at the N_v centroids, natural order
+ * (used by the self term, Appendix A). */
+typedef struct {
+  int n_I;
+  const double* nodes_x;
+  const double* nodes_y;
+  const double* tau2;
+  const double* v0;
+  const double* v1;
+  const double* n_cells;
+} hb_tables;
+
+/* Construction options (Sec. 4.2).  eps: relative tolerance of the ID
+ * (Eq. ID); leaf: maximum cluster-tree leaf size; chi: oversampling of the
+ * uniform proxy rows and nbr_radius_h: neighbour radius in units of h
+ * (Eq. proxyv2v); precision: HB_FP64 or HB_MIXED_BF16X3 for hb_apply /
+ * hb_apply_adjoint; workspace_mb: device workspace bound for the build
+ * (0 = default); barrier_cycles: spin budget of bounded device waits
+ * (0 = default). */
+typedef struct {
+  double eps;
+  int leaf;
+  double chi;
+  double nbr_radius_h;
+  int precision;
+  int workspace_mb;
+  long long barrier_cycles;
+} hb_options;
+
+/* Statistics filled by hb_info. */
+typedef struct {
+  long long n_v;
+  int levels;                 /* L_v of the cluster tree                    */
+  int max_rank;               /* largest butterfly rank r_{tau,nu}          */
+  long long factor_entries;   /* complex entries of all factors + leaves    */
+  long long factor_bytes_fp64;
+  long long factor_bytes_mixed;
+  long long id_blocks;        /* interpolative decompositions computed      */
+  long long sampled_entries;  /* matrix entries evaluated by the build      */
+  double build_ms;
+  int built;
+  int apply_launches;         /* kernels launched by one hb_apply           */
+  long long skeleton_rows;    /* sum of all ranks: rows of skeleton vectors */
+} hb_stats;
+
+/* hb_create: validate and copy the grid, tables and options; upload the
+ * tables; precompute the Lagrange interpolants at the cell coordinates and
+ * the self terms K_ii (Appendix A).  Synchronous.  On success *out owns
+ * device memory until hb_destroy.  Errors: HB_ERR_ARG for invalid input
+ * (non-positive sizes, n_I < 2 or > 32, omega <= 0, eps <= 0, leaf < 1),
+ * HB_ERR_OOM, HB_ERR_CUDA. */
+hb_status hb_create(const hb_grid* grid, const hb_tables* tables, double omega,
+                    const hb_options* opts, hb_handle* out);
+
+/* hb_build: construct the HODBF representation (Sec. 4.2): K-D cluster tree,
+ * per butterfly level proxy rows (Eq. proxyv2v, host), sampled blocks
+ * (device, Eq. chebinterpblock + Eq. babich), batched CPQR interpolative
+ * decompositions (device, Eq. ID / Eq. proxy), skeleton factors K^L and
+ * dense leaf blocks; packs the factors for the FP64 and mixed applies.
+ * Synchronous.  Errors: HB_ERR_OOM, HB_ERR_CUDA, HB_ERR_STATE if built. */
+hb_status hb_build(hb_handle h);
+
+/* hb_apply: u = K (h^2 s) with the compressed operator (Eq. butterfly_mat
+ * summed over the HODBF, plus the dense leaf blocks), in the precision of
+ * opts.precision (see hb_set_precision).  s, u: device, complex128,
+ * N_v x nrhs column-major, must not overlap.  1 <= nrhs <= 1024.
+ * Errors: HB_ERR_STATE before hb_build, HB_ERR_ARG, HB_ERR_CUDA. */
+hb_status hb_apply(hb_handle h, const void* s, void* u, int nrhs, void* stream);
+
+/* hb_apply_adjoint: s = h^2 K~^H u, the exact adjoint of hb_apply's
+ * compressed operator K~ (reversed factor order, conjugate-transposed
+ * blocks).  Same layout, limits and errors as hb_apply. */
+hb_status hb_apply_adjoint(hb_handle h, const void* u, void* s, int nrhs, void* stream);
+
+/* hb_set_precision: HB_FP64 or HB_MIXED_BF16X3 for later applies. */
+hb_status hb_set_precision(hb_handle h, int precision);
+
+/* hb_apply_dense / hb_apply_dense_adjoint: the same sums (Eq. m_v2v) and
+ * their adjoint, matrix free, every entry evaluated in FP64 on the fly
+ * (Eq. chebinterpblock, Eq. babich, Appendix A).  Needs no hb_build.
+ * Same layout and limits as hb_apply. */
+hb_status hb_apply_dense(hb_handle h, const void* s, void* u, int nrhs, void* stream);
+hb_status hb_apply_dense_adjoint(hb_handle h, const void* u, void* s, int nrhs, void* stream);
+
+/* hb_entries: K[rows, cols] for index lists (natural order, int64, HOST
+ * arrays), written as an m x n complex128 column-major DEVICE array `out`
+ * (Eq. chebinterpblock + Eq. babich; diagonal pairs rows[a] == cols[b] give
+ * the self term of Appendix A).  Synchronous.  Errors: HB_ERR_ARG for
+ * m, n < 1 or an index outside [0, N_v). */
+hb_status hb_entries(hb_handle h, const long long* rows, int m, const long long* cols,
+                     int n, void* out, void* stream);
+
+/* hb_id_batch: batched column-pivoted QR interpolative decompositions
+ * (Eq. ID) of `count` complex128 matrices, with the same rules as the build:
+ * pivot on the largest recomputed trailing column norm (lowest index on exact
+ * ties), rank = first k >= 1 with |R_kk| <= eps |R_00|, V = [I | R11^-1 R12] P^T.
+ * A: DEVICE, matrix b is m[b] x n[b] column-major at element offset a_off[b];
+ * it is overwritten.  m, n, a_off: HOST arrays of length count.
+ * Outputs (DEVICE): rank[b]; skel + sum_{c<b} n[c]: the rank[b] skeleton
+ * column indices in pivot order; V + sum_{c<b} n[c]^2: the rank x n[b]
+ * matrix V, column-major with leading dimension n[b].  Synchronous. */
+hb_status hb_id_batch(int count, const int* m, const int* n, const long long* a_off,
+                      void* A, double eps, int* rank, int* skel, void* V);
+
+/* hb_tree_perm: copy the cluster-tree permutation (tree position ->
+ * natural index, N_v int64) to a HOST array.  Valid after hb_create. */
+hb_status hb_tree_perm(hb_handle h, long long* perm_out);
+
+/* hb_proxy_rows: the proxy-row rule Eq. proxyv2v for the row node
+ * tau = tree positions [t0, t1) and seed columns `seeds` (tree positions,
+ * HOST).  Writes the sorted proxy tree positions to the HOST array out
+ * (capacity t1 - t0) and their number to *count. */
+hb_status hb_proxy_rows(hb_handle h, long long t0, long long t1, const long long* seeds,
+                        int nseeds, long long* out, long long* count);
+
+hb_status hb_info(hb_handle h, hb_stats* stats);
+
+/* hb_kernel_times: enable (1) / disable (0) CUDA-event timing of every
+ * kernel launched by hb_apply / hb_apply_adjoint on the launch stream, and
+ * read back the accumulated per-kernel-group totals: names, total ms and
+ * launch counts for up to `cap` groups (HOST arrays); *ngroups receives the
+ * number of groups.  Reading resets the totals.  Synchronous. */
+hb_status hb_set_kernel_timing(hb_handle h, int enable);
+hb_status hb_kernel_times(hb_handle h, int cap, char (*names)[32], double* total_ms,
+                          long long* launches, int* ngroups);
+
+const char* hb_last_error(hb_handle h);
+void hb_destroy(hb_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HB_H_ */

@@ -1,0 +1,223 @@
+"""ctypes binding of the C ABI declared in ``include/hb.h``.
+
+Argument marshalling only: every computation runs in ``_lib/libhb.so``.
+Tensors passed in are used through their data pointers (``torch.Tensor``
+on CUDA for vectors, host numpy arrays for tables and index lists).
+``lib()`` raises if the library is missing - there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libhb.so")
+
+HB_OK, HB_ERR_ARG, HB_ERR_CUDA, HB_ERR_OOM, HB_ERR_TIMEOUT, HB_ERR_STATE, HB_ERR_UNSUPPORTED = range(7)
+HB_FP64, HB_MIXED_BF16X3 = 0, 1
+STATUS = {0: "HB_OK", 1: "HB_ERR_ARG", 2: "HB_ERR_CUDA", 3: "HB_ERR_OOM", 4: "HB_ERR_TIMEOUT",
+          5: "HB_ERR_STATE", 6: "HB_ERR_UNSUPPORTED"}
+
+# every symbol include/hb.h declares
+EXPORTS = ["hb_create", "hb_build", "hb_apply", "hb_apply_adjoint", "hb_set_precision",
+           "hb_apply_dense", "hb_apply_dense_adjoint", "hb_entries", "hb_id_batch",
+           "hb_tree_perm", "hb_proxy_rows", "hb_info", "hb_set_kernel_timing",
+           "hb_kernel_times", "hb_last_error", "hb_destroy"]
+
+
+class Grid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("x0", C.c_double), ("y0", C.c_double),
+                ("h", C.c_double)]
+
+
+class Tables(C.Structure):
+    _fields_ = [("n_I", C.c_int), ("nodes_x", C.c_void_p), ("nodes_y", C.c_void_p),
+                ("tau2", C.c_void_p), ("v0", C.c_void_p), ("v1", C.c_void_p),
+                ("n_cells", C.c_void_p)]
+
+
+class Options(C.Structure):
+    _fields_ = [("eps", C.c_double), ("leaf", C.c_int), ("chi", C.c_double),
+                ("nbr_radius_h", C.c_double), ("precision", C.c_int), ("workspace_mb", C.c_int),
+                ("barrier_cycles", C.c_longlong)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("n_v", C.c_longlong), ("levels", C.c_int), ("max_rank", C.c_int),
+                ("factor_entries", C.c_longlong), ("factor_bytes_fp64", C.c_longlong),
+                ("factor_bytes_mixed", C.c_longlong), ("id_blocks", C.c_longlong),
+                ("sampled_entries", C.c_longlong), ("build_ms", C.c_double), ("built", C.c_int),
+                ("apply_launches", C.c_int), ("skeleton_rows", C.c_longlong)]
+
+
+_LIB = None
+
+
+def lib():
+    """Load libhb.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} missing: run paper_2210_02698_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        vp, i, d, ll = C.c_void_p, C.c_int, C.c_double, C.c_longlong
+        L.hb_create.argtypes = [C.POINTER(Grid), C.POINTER(Tables), d, C.POINTER(Options), C.POINTER(vp)]
+        L.hb_build.argtypes = [vp]
+        for f in ("hb_apply", "hb_apply_adjoint", "hb_apply_dense", "hb_apply_dense_adjoint"):
+            getattr(L, f).argtypes = [vp, vp, vp, i, vp]
+        L.hb_set_precision.argtypes = [vp, i]
+        L.hb_entries.argtypes = [vp, vp, i, vp, i, vp, vp]
+        L.hb_id_batch.argtypes = [i, vp, vp, vp, vp, d, vp, vp, vp]
+        L.hb_tree_perm.argtypes = [vp, vp]
+        L.hb_proxy_rows.argtypes = [vp, ll, ll, vp, i, vp, vp]
+        L.hb_info.argtypes = [vp, C.POINTER(Stats)]
+        L.hb_set_kernel_timing.argtypes = [vp, i]
+        L.hb_kernel_times.argtypes = [vp, i, vp, vp, vp, vp]
+        L.hb_last_error.argtypes = [vp]
+        L.hb_last_error.restype = C.c_char_p
+        L.hb_destroy.argtypes = [vp]
+        L.hb_destroy.restype = None
+        for f in EXPORTS:
+            if f not in ("hb_last_error", "hb_destroy"):
+                getattr(L, f).restype = C.c_int
+        _LIB = L
+    return _LIB
+
+
+class HBError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(st, handle=None):
+    if st != HB_OK:
+        raise HBError(st, lib().hb_last_error(handle).decode(errors="replace"))
+
+
+def _ptr(t):
+    """Device/host address of a torch tensor or numpy array."""
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr()
+    return t.ctypes.data
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    return getattr(stream, "cuda_stream", stream)
+
+
+class Operator:
+    """Handle owning one discretised HB operator (hb_create .. hb_destroy)."""
+
+    def __init__(self, N, nodes, tau2, v0, v1, n_cells, omega, eps=1e-6, leaf=64, chi=20.0,
+                 nbr_radius_h=10.0, precision=HB_MIXED_BF16X3, workspace_mb=0, h=None,
+                 x0=0.0, y0=0.0):
+        L = lib()
+        self._keep = [np.ascontiguousarray(a, dtype=np.float64) for a in (nodes, tau2, v0, v1, n_cells)]
+        nodes, tau2, v0, v1, n_cells = self._keep
+        nx, ny = (N, N) if np.isscalar(N) else N
+        self.nx, self.ny = nx, ny
+        self.Nv = nx * ny
+        self.h = (1.0 / nx) if h is None else h
+        g = Grid(nx, ny, x0, y0, self.h)
+        t = Tables(len(nodes), nodes.ctypes.data, nodes.ctypes.data, tau2.ctypes.data,
+                   v0.ctypes.data, v1.ctypes.data, n_cells.ctypes.data)
+        o = Options(eps, leaf, chi, nbr_radius_h, precision, workspace_mb, 0)
+        hnd = C.c_void_p()
+        _check(L.hb_create(C.byref(g), C.byref(t), float(omega), C.byref(o), C.byref(hnd)))
+        self.handle = hnd
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().hb_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _call(self, name, *args):
+        _check(getattr(lib(), name)(self.handle, *args), self.handle)
+
+    def build(self):
+        self._call("hb_build")
+
+    def set_precision(self, p):
+        self._call("hb_set_precision", int(p))
+
+    def apply(self, s, u, nrhs, stream=None):
+        self._call("hb_apply", _ptr(s), _ptr(u), int(nrhs), _stream_ptr(stream))
+
+    def apply_adjoint(self, u, s, nrhs, stream=None):
+        self._call("hb_apply_adjoint", _ptr(u), _ptr(s), int(nrhs), _stream_ptr(stream))
+
+    def apply_dense(self, s, u, nrhs, stream=None):
+        self._call("hb_apply_dense", _ptr(s), _ptr(u), int(nrhs), _stream_ptr(stream))
+
+    def apply_dense_adjoint(self, u, s, nrhs, stream=None):
+        self._call("hb_apply_dense_adjoint", _ptr(u), _ptr(s), int(nrhs), _stream_ptr(stream))
+
+    def entries(self, rows, cols, out, stream=None):
+        rows = np.ascontiguousarray(rows, dtype=np.int64)
+        cols = np.ascontiguousarray(cols, dtype=np.int64)
+        self._call("hb_entries", rows.ctypes.data, len(rows), cols.ctypes.data, len(cols), _ptr(out),
+                   _stream_ptr(stream))
+
+    def tree_perm(self):
+        out = np.empty(self.Nv, dtype=np.int64)
+        self._call("hb_tree_perm", out.ctypes.data)
+        return out
+
+    def proxy_rows(self, t0, t1, seeds):
+        seeds = np.ascontiguousarray(seeds, dtype=np.int64)
+        out = np.empty(max(t1 - t0, 1), dtype=np.int64)
+        cnt = C.c_longlong()
+        self._call("hb_proxy_rows", int(t0), int(t1), seeds.ctypes.data, len(seeds), out.ctypes.data,
+                   C.byref(cnt))
+        return out[:cnt.value].copy()
+
+    def info(self):
+        s = Stats()
+        self._call("hb_info", C.byref(s))
+        return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+    def set_kernel_timing(self, on):
+        self._call("hb_set_kernel_timing", 1 if on else 0)
+
+    def kernel_times(self):
+        cap = 32
+        names = (C.c_char * 32 * cap)()
+        ms = (C.c_double * cap)()
+        cnt = (C.c_longlong * cap)()
+        ng = C.c_int()
+        self._call("hb_kernel_times", cap, C.cast(names, C.c_void_p), C.cast(ms, C.c_void_p),
+                   C.cast(cnt, C.c_void_p), C.byref(ng))
+        return {bytes(names[i]).split(b"\0")[0].decode(): (ms[i], cnt[i]) for i in range(min(ng.value, cap))}
+
+
+def id_batch(A, m, n, a_off, eps, rank, skel, V):
+    """hb_id_batch on device buffers (torch tensors) with host size arrays."""
+    m = np.ascontiguousarray(m, dtype=np.int32)
+    n = np.ascontiguousarray(n, dtype=np.int32)
+    a_off = np.ascontiguousarray(a_off, dtype=np.int64)
+    _check(lib().hb_id_batch(len(m), m.ctypes.data, n.ctypes.data, a_off.ctypes.data, _ptr(A),
+                             float(eps), _ptr(rank), _ptr(skel), _ptr(V)))
+
+
+def load_tables(path):
+    z = np.load(path)
+    return z["nodes"], z["tau2"], z["v0"], z["v1"]
+
+
+def operator_for(workload, tables_path, precision=HB_MIXED_BF16X3, **kw):
+    """Operator of a workloads.Workload with tables from a stored .npz file."""
+    nodes, t2, v0, v1 = load_tables(tables_path)
+    return Operator(workload.N, nodes, t2, v0, v1, workload.n_cells(), workload.omega,
+                    eps=kw.pop("eps", workload.eps), leaf=kw.pop("leaf", workload.leaf),
+                    chi=kw.pop("chi", workload.chi), precision=precision, **kw)

@@ -1,0 +1,269 @@
+// api.cu - the extern "C" entry points declared in include/hb.h.  Argument
+// checks, error capture (no exception crosses the ABI) and dispatch to the
+// kernels of entries.cu, cpqr.cu, build.cu and apply.cu.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "hb_internal.cuh"
+
+namespace {
+
+thread_local std::string g_err;   // errors of calls without a handle
+
+template <class F>
+hb_status guarded(hb_ctx* c, F&& f) {
+  try {
+    f();
+    return HB_OK;
+  } catch (const hb::Error& e) {
+    (c ? c->err : g_err) = e.msg;
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    (c ? c->err : g_err) = "host allocation failed";
+    return HB_ERR_OOM;
+  } catch (...) {
+    (c ? c->err : g_err) = "unexpected C++ exception";
+    return HB_ERR_CUDA;
+  }
+}
+
+void free_all(hb_ctx* c) {
+  for (void* p : {(void*)c->d_nodes, (void*)c->d_tab, (void*)c->d_LX, (void*)c->d_LZ, (void*)c->d_H[0],
+                  (void*)c->d_H[1], (void*)c->d_ncell, (void*)c->d_self, (void*)c->d_perm, (void*)c->d_f64,
+                  (void*)c->d_f32, c->d_x, c->d_y})
+    hb::dev_free(p);
+  hb::dev_free(c->d_xh);
+  hb::dev_free(c->d_tasks[0]);
+  hb::dev_free(c->d_tasks[1]);
+}
+
+void check_vec_args(hb_ctx* c, const void* a, const void* b, int nrhs) {
+  if (!c) throw hb::arg_error("null handle");
+  if (!a || !b) throw hb::arg_error("null vector pointer");
+  if (a == b) throw hb::arg_error("input and output must not alias");
+  if (nrhs < 1 || nrhs > 1024) throw hb::arg_error("nrhs=%d outside [1, 1024]", nrhs);
+}
+
+}  // namespace
+
+extern "C" {
+
+hb_status hb_create(const hb_grid* grid, const hb_tables* tables, double omega, const hb_options* opts,
+                    hb_handle* out) {
+  hb_ctx* c = nullptr;
+  hb_status st = guarded(nullptr, [&] {
+    if (!grid || !tables || !opts || !out) throw hb::arg_error("null argument");
+    *out = nullptr;
+    if (grid->nx < 1 || grid->ny < 1 || !(grid->h > 0)) throw hb::arg_error("bad grid");
+    if ((long long)grid->nx * grid->ny > (1LL << 31)) throw hb::arg_error("grid too large");
+    if (tables->n_I < 2 || tables->n_I > 16)
+      throw hb::Error{tables->n_I < 2 ? HB_ERR_ARG : HB_ERR_UNSUPPORTED, "n_I must be in [2, 16]"};
+    if (!tables->nodes_x || !tables->nodes_y || !tables->tau2 || !tables->v0 || !tables->v1 ||
+        !tables->n_cells)
+      throw hb::arg_error("null table pointer");
+    if (!(omega > 0) || !std::isfinite(omega)) throw hb::arg_error("omega must be positive");
+    if (!(opts->eps > 0) || opts->leaf < 1 || !(opts->chi > 0) || !(opts->nbr_radius_h >= 0))
+      throw hb::arg_error("bad options (eps > 0, leaf >= 1, chi > 0, radius >= 0)");
+    if (opts->precision != HB_FP64 && opts->precision != HB_MIXED_BF16X3)
+      throw hb::arg_error("unknown precision %d", opts->precision);
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+      cudaGetLastError();
+      throw hb::Error{HB_ERR_CUDA, "no CUDA device"};
+    }
+    c = new hb_ctx();
+    c->nx = grid->nx;
+    c->ny = grid->ny;
+    c->Nv = (long long)grid->nx * grid->ny;
+    c->x0 = grid->x0;
+    c->y0 = grid->y0;
+    c->h = grid->h;
+    c->omega = omega;
+    c->nI = tables->n_I;
+    c->NI = tables->n_I * tables->n_I;
+    c->opt = *opts;
+    c->nodes_x.assign(tables->nodes_x, tables->nodes_x + c->nI);
+    c->nodes_y.assign(tables->nodes_y, tables->nodes_y + c->nI);
+    const double* src[3] = {tables->tau2, tables->v0, tables->v1};
+    for (int q = 0; q < 3; ++q) c->tab[q].assign(src[q], src[q] + (size_t)c->NI * c->NI);
+    c->n_cells.assign(tables->n_cells, tables->n_cells + c->Nv);
+    for (double v : c->n_cells)
+      if (!(v > 0) || !std::isfinite(v)) throw hb::arg_error("n_cells must be positive");
+    hb::setup_tables(c);
+    hb::tree_build(c);
+    c->stats.n_v = c->Nv;
+    c->stats.levels = c->Lv;
+  });
+  if (st != HB_OK) {
+    if (c) {
+      g_err = c->err;
+      free_all(c);
+      delete c;
+    }
+    return st;
+  }
+  *out = c;
+  return HB_OK;
+}
+
+hb_status hb_build(hb_handle h) {
+  return guarded(h, [&] {
+    if (!h) throw hb::arg_error("null handle");
+    if (h->built) throw hb::Error{HB_ERR_STATE, "already built"};
+    hb::build(h);
+    h->built = true;
+  });
+}
+
+hb_status hb_apply(hb_handle h, const void* s, void* u, int nrhs, void* stream) {
+  return guarded(h, [&] {
+    check_vec_args(h, s, u, nrhs);
+    if (!h->built) throw hb::Error{HB_ERR_STATE, "hb_apply before hb_build"};
+    hb::apply_bf(h, (const double2*)s, (double2*)u, nrhs, 0, h->opt.precision, (cudaStream_t)stream);
+  });
+}
+
+hb_status hb_apply_adjoint(hb_handle h, const void* u, void* s, int nrhs, void* stream) {
+  return guarded(h, [&] {
+    check_vec_args(h, u, s, nrhs);
+    if (!h->built) throw hb::Error{HB_ERR_STATE, "hb_apply_adjoint before hb_build"};
+    hb::apply_bf(h, (const double2*)u, (double2*)s, nrhs, 1, h->opt.precision, (cudaStream_t)stream);
+  });
+}
+
+hb_status hb_set_precision(hb_handle h, int precision) {
+  return guarded(h, [&] {
+    if (!h) throw hb::arg_error("null handle");
+    if (precision != HB_FP64 && precision != HB_MIXED_BF16X3) throw hb::arg_error("unknown precision");
+    h->opt.precision = precision;
+  });
+}
+
+hb_status hb_apply_dense(hb_handle h, const void* s, void* u, int nrhs, void* stream) {
+  return guarded(h, [&] {
+    check_vec_args(h, s, u, nrhs);
+    hb::dense_apply(h, (const double2*)s, (double2*)u, nrhs, 0, (cudaStream_t)stream);
+  });
+}
+
+hb_status hb_apply_dense_adjoint(hb_handle h, const void* u, void* s, int nrhs, void* stream) {
+  return guarded(h, [&] {
+    check_vec_args(h, u, s, nrhs);
+    hb::dense_apply(h, (const double2*)u, (double2*)s, nrhs, 1, (cudaStream_t)stream);
+  });
+}
+
+hb_status hb_entries(hb_handle h, const long long* rows, int m, const long long* cols, int n, void* out,
+                     void* stream) {
+  return guarded(h, [&] {
+    if (!h || !rows || !cols || !out) throw hb::arg_error("null argument");
+    if (m < 1 || n < 1) throw hb::arg_error("m, n must be >= 1");
+    for (int i = 0; i < m; ++i)
+      if (rows[i] < 0 || rows[i] >= h->Nv) throw hb::arg_error("row index %lld out of range", rows[i]);
+    for (int j = 0; j < n; ++j)
+      if (cols[j] < 0 || cols[j] >= h->Nv) throw hb::arg_error("column index %lld out of range", cols[j]);
+    hb::eval_entries(h, rows, m, cols, n, (double2*)out, (cudaStream_t)stream);
+  });
+}
+
+hb_status hb_id_batch(int count, const int* m, const int* n, const long long* a_off, void* A, double eps,
+                      int* rank, int* skel, void* V) {
+  return guarded(nullptr, [&] {
+    if (count < 0 || (count > 0 && (!m || !n || !a_off || !A || !rank || !skel || !V)))
+      throw hb::arg_error("bad hb_id_batch arguments");
+    if (!(eps >= 0)) throw hb::arg_error("eps must be >= 0");
+    if (count == 0) return;
+    std::vector<long long> soff(count), voff(count);
+    long long sacc = 0, vacc = 0;
+    int max_n = 0;
+    for (int b = 0; b < count; ++b) {
+      if (m[b] < 1 || n[b] < 1) throw hb::arg_error("matrix %d has an empty dimension", b);
+      soff[b] = sacc;
+      voff[b] = vacc;
+      sacc += n[b];
+      vacc += (long long)n[b] * n[b];
+      max_n = std::max(max_n, n[b]);
+    }
+    int* d_m = hb::upload(std::vector<int>(m, m + count));
+    int* d_n = hb::upload(std::vector<int>(n, n + count));
+    long long* d_a = hb::upload(std::vector<long long>(a_off, a_off + count));
+    long long* d_s = hb::upload(soff);
+    long long* d_v = hb::upload(voff);
+    int* d_perm = hb::dev_alloc<int>(sacc);
+    hb::id_batch(count, d_m, d_n, d_a, (double2*)A, eps, rank, d_perm, d_s, max_n, 0);
+    hb::emit_v(count, d_m, d_n, d_a, (const double2*)A, rank, d_perm, d_s, d_v, 0, (double2*)V, nullptr, 0);
+    HB_CUDA(cudaMemcpy(skel, d_perm, sizeof(int) * sacc, cudaMemcpyDeviceToDevice));
+    HB_CUDA(cudaDeviceSynchronize());
+    hb::dev_free(d_perm);
+    for (void* p : {(void*)d_m, (void*)d_n, (void*)d_a, (void*)d_s, (void*)d_v}) hb::dev_free(p);
+  });
+}
+
+hb_status hb_tree_perm(hb_handle h, long long* perm_out) {
+  return guarded(h, [&] {
+    if (!h || !perm_out) throw hb::arg_error("null argument");
+    std::memcpy(perm_out, h->perm.data(), sizeof(long long) * h->Nv);
+  });
+}
+
+hb_status hb_proxy_rows(hb_handle h, long long t0, long long t1, const long long* seeds, int nseeds,
+                        long long* out, long long* count) {
+  return guarded(h, [&] {
+    if (!h || !out || !count || (nseeds > 0 && !seeds)) throw hb::arg_error("null argument");
+    if (t0 < 0 || t1 > h->Nv || t0 >= t1) throw hb::arg_error("bad range");
+    for (int s = 0; s < nseeds; ++s)
+      if (seeds[s] < 0 || seeds[s] >= h->Nv) throw hb::arg_error("seed out of range");
+    std::vector<long long> rows;
+    std::vector<int> stamp((size_t)h->Nv, -1);
+    hb::proxy_rows(h, t0, t1, seeds, nseeds, rows, stamp, 1);
+    std::memcpy(out, rows.data(), sizeof(long long) * rows.size());
+    *count = (long long)rows.size();
+  });
+}
+
+hb_status hb_info(hb_handle h, hb_stats* stats) {
+  return guarded(h, [&] {
+    if (!h || !stats) throw hb::arg_error("null argument");
+    *stats = h->stats;
+    stats->built = h->built ? 1 : 0;
+  });
+}
+
+hb_status hb_set_kernel_timing(hb_handle h, int enable) {
+  return guarded(h, [&] {
+    if (!h) throw hb::arg_error("null handle");
+    h->timing = enable != 0;
+  });
+}
+
+hb_status hb_kernel_times(hb_handle h, int cap, char (*names)[32], double* total_ms, long long* launches,
+                          int* ngroups) {
+  return guarded(h, [&] {
+    if (!h || !ngroups || (cap > 0 && (!names || !total_ms || !launches))) throw hb::arg_error("null argument");
+    int n = (int)h->tnames.size();
+    *ngroups = n;
+    for (int i = 0; i < n && i < cap; ++i) {
+      std::strncpy(names[i], h->tnames[i].c_str(), 31);
+      names[i][31] = 0;
+      total_ms[i] = h->tms[i];
+      launches[i] = h->tcount[i];
+    }
+    for (auto& v : h->tms) v = 0;
+    for (auto& v : h->tcount) v = 0;
+  });
+}
+
+const char* hb_last_error(hb_handle h) { return h ? h->err.c_str() : g_err.c_str(); }
+
+void hb_destroy(hb_handle h) {
+  if (!h) return;
+  free_all(h);
+  delete h;
+}
+
+}  // extern "C"

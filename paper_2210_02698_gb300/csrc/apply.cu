@@ -1,0 +1,218 @@
+// apply.cu - butterfly / HODBF apply and its adjoint on the device
+// (Sec. 4.2.1, Eq. butterfly_mat, Eq. butterfly_factors; Sec. 4.2 HODBF).
+//
+//   x  = h^2 s, gathered into cluster-tree order            (Eq. m_v2v)
+//   steps of small dense products over all butterflies      (build.cu plans)
+//   u  = y scattered back to natural order
+//
+// FP64 path: complex128 factors and vectors, one CTA per task, plain FP64
+// FMAs (the baseline).  Mixed path (HB_MIXED_BF16X3): FP32 factors and
+// vectors; see bf_mma.cu for the tensor-core step kernel.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "hb_internal.cuh"
+
+namespace hb {
+
+__global__ void f64_to_f32_kernel(const double2* __restrict__ a, float2* __restrict__ b, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    b[i] = make_float2((float)a[i].x, (float)a[i].y);
+}
+
+void convert_f64_f32(const double2* a, float2* b, long long n, cudaStream_t st) {
+  if (n <= 0) return;
+  f64_to_f32_kernel<<<1216, 256, 0, st>>>(a, b, n);
+  HB_CHECK_LAUNCH();
+}
+
+template <class C>
+struct Real;
+template <>
+struct Real<double2> {
+  using T = double;
+  static __device__ __forceinline__ double2 make(double x, double y) { return make_double2(x, y); }
+};
+template <>
+struct Real<float2> {
+  using T = float;
+  static __device__ __forceinline__ float2 make(float x, float y) { return make_float2(x, y); }
+};
+
+// x[p][r] = scale * s[r*Nv + perm[p]]   (column-major natural -> row-major tree order)
+template <class C>
+__global__ void gather_kernel(const double2* __restrict__ s, const long long* __restrict__ perm, C* __restrict__ x,
+                              long long Nv, int R, double scale) {
+  long long total = Nv * R;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    long long p = idx / R;
+    int r = (int)(idx % R);
+    double2 v = s[(size_t)r * Nv + perm[p]];
+    x[idx] = Real<C>::make((typename Real<C>::T)(v.x * scale), (typename Real<C>::T)(v.y * scale));
+  }
+}
+
+template <class C>
+__global__ void scatter_kernel(const C* __restrict__ y, const long long* __restrict__ perm, double2* __restrict__ u,
+                               long long Nv, int R) {
+  long long total = Nv * R;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    long long p = idx / R;
+    int r = (int)(idx % R);
+    C v = y[idx];
+    u[(size_t)r * Nv + perm[p]] = make_double2((double)v.x, (double)v.y);
+  }
+}
+
+// One CTA per task; thread -> (output row, right-hand side), rows fastest.
+template <class C>
+__global__ void __launch_bounds__(128) step_kernel(const Task* __restrict__ tasks, const C* __restrict__ F,
+                                                   C* __restrict__ x, C* __restrict__ y, C* __restrict__ xh,
+                                                   int R) {
+  using T = typename Real<C>::T;
+  const Task tk = tasks[blockIdx.x];
+  C* bufs[3] = {x, y, xh};
+  C* out = bufs[tk.y_buf] + (size_t)tk.y_off * R;
+  const int total = tk.r_out * R;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int row = idx % tk.r_out, rr = idx / tk.r_out;
+    T ar = 0, ai = 0;
+    for (int t = 0; t < tk.nterm; ++t) {
+      const C* f = F + tk.f_off[t];
+      const C* xin = bufs[tk.x_buf] + (size_t)tk.x_off[t] * R + rr;
+      const int rin = tk.r_in[t];
+      if (!tk.conj_t) {
+        for (int k = 0; k < rin; ++k) {
+          const C a = f[(size_t)k * tk.r_out + row];
+          const C v = xin[(size_t)k * R];
+          ar = fma(a.x, v.x, fma(-a.y, v.y, ar));
+          ai = fma(a.x, v.y, fma(a.y, v.x, ai));
+        }
+      } else {
+        const C* fr = f + (size_t)row * rin;
+        for (int k = 0; k < rin; ++k) {
+          const C a = fr[k];
+          const C v = xin[(size_t)k * R];
+          ar = fma(a.x, v.x, fma(a.y, v.y, ar));     // conj(a) v
+          ai = fma(a.x, v.y, fma(-a.y, v.x, ai));
+        }
+      }
+    }
+    C* o = out + (size_t)row * R + rr;
+    if (tk.accumulate) {
+      C prev = *o;
+      ar += prev.x;
+      ai += prev.y;
+    }
+    *o = Real<C>::make(ar, ai);
+  }
+}
+
+namespace {
+
+struct TimerScope {
+  hb_ctx* c;
+  cudaStream_t st;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
+  int group(const char* name) {
+    for (size_t i = 0; i < c->tnames.size(); ++i)
+      if (c->tnames[i] == name) return (int)i;
+    c->tnames.push_back(name);
+    c->tms.push_back(0);
+    c->tcount.push_back(0);
+    return (int)c->tnames.size() - 1;
+  }
+  void begin(const char* name) {
+    if (!c->timing) return;
+    cudaEvent_t a, b;
+    HB_CUDA(cudaEventCreate(&a));
+    HB_CUDA(cudaEventCreate(&b));
+    HB_CUDA(cudaEventRecord(a, st));
+    ev.push_back({group(name), {a, b}});
+  }
+  void end() {
+    if (!c->timing) return;
+    HB_CUDA(cudaEventRecord(ev.back().second.second, st));
+  }
+  void finish() {
+    if (!c->timing) return;
+    HB_CUDA(cudaStreamSynchronize(st));
+    for (auto& e : ev) {
+      float ms = 0;
+      HB_CUDA(cudaEventElapsedTime(&ms, e.second.first, e.second.second));
+      c->tms[e.first] += ms;
+      c->tcount[e.first] += 1;
+      cudaEventDestroy(e.second.first);
+      cudaEventDestroy(e.second.second);
+    }
+    ev.clear();
+  }
+};
+
+void ensure_scratch(hb_ctx* c, int nrhs) {
+  if (c->cap_rhs >= nrhs) return;
+  dev_free(c->d_x);
+  dev_free(c->d_y);
+  dev_free(c->d_xh);
+  c->d_x = c->d_y = c->d_xh = nullptr;
+  c->cap_rhs = 0;
+  c->d_x = dev_alloc<double2>((size_t)c->Nv * nrhs);
+  c->d_y = dev_alloc<double2>((size_t)c->Nv * nrhs);
+  c->d_xh = dev_alloc<double2>((size_t)std::max<long long>(c->xh_rows, 1) * nrhs);
+  c->cap_rhs = nrhs;
+  if (!c->d_perm) c->d_perm = upload(c->perm);
+  HB_CUDA(cudaDeviceSynchronize());
+}
+
+template <class C>
+void run_steps(hb_ctx* c, const C* F, int nrhs, int dir, cudaStream_t st, TimerScope& ts) {
+  const std::vector<int>& sb = c->step_begin[dir];
+  for (size_t s = 0; s + 1 < sb.size(); ++s) {
+    int n = sb[s + 1] - sb[s];
+    if (n == 0) continue;
+    ts.begin(dir ? "bf_step_adjoint" : "bf_step");
+    step_kernel<C><<<n, 128, 0, st>>>(c->d_tasks[dir] + sb[s], F, (C*)c->d_x, (C*)c->d_y, (C*)c->d_xh, nrhs);
+    HB_CHECK_LAUNCH();
+    ts.end();
+  }
+}
+
+}  // namespace
+
+void apply_bf(hb_ctx* c, const double2* s, double2* u, int nrhs, int adjoint, int precision, cudaStream_t st) {
+  ensure_scratch(c, nrhs);
+  TimerScope ts{c, st, {}};
+  const long long total = c->Nv * nrhs;
+  const int grid = (int)std::min<long long>((total + 255) / 256, 152LL * 16);
+  const double scale = c->h * c->h;
+  if (precision == HB_FP64) {
+    ts.begin("gather");
+    gather_kernel<double2><<<grid, 256, 0, st>>>(s, c->d_perm, (double2*)c->d_x, c->Nv, nrhs, scale);
+    HB_CHECK_LAUNCH();
+    ts.end();
+    run_steps<double2>(c, c->d_f64, nrhs, adjoint, st, ts);
+    ts.begin("scatter");
+    scatter_kernel<double2><<<grid, 256, 0, st>>>((double2*)c->d_y, c->d_perm, u, c->Nv, nrhs);
+    HB_CHECK_LAUNCH();
+    ts.end();
+  } else {
+    ts.begin("gather");
+    gather_kernel<float2><<<grid, 256, 0, st>>>(s, c->d_perm, (float2*)c->d_x, c->Nv, nrhs, scale);
+    HB_CHECK_LAUNCH();
+    ts.end();
+    run_steps<float2>(c, c->d_f32, nrhs, adjoint, st, ts);
+    ts.begin("scatter");
+    scatter_kernel<float2><<<grid, 256, 0, st>>>((float2*)c->d_y, c->d_perm, u, c->Nv, nrhs);
+    HB_CHECK_LAUNCH();
+    ts.end();
+  }
+  ts.finish();
+}
+
+}  // namespace hb

@@ -1,0 +1,462 @@
+// build.cu - host orchestration of the HODBF / butterfly construction
+// (Sec. 4.2, Sec. 4.2.1, Eq. transfer_computation, Eq. proxy,
+// Eq. butterfly_factors, Eq. proxyv2v) and of the apply task plans.
+//
+// HODBF (Sec. 4.2, K^{v2v} item): for siblings tau1, tau2 at level l of the
+// cluster tree, K(tau1, tau2) and K(tau2, tau1) are butterflies with
+// L = L_v - l levels; the 2^{L_v} leaf diagonal blocks stay dense.
+// Construction runs butterfly level by butterfly level for all butterflies
+// at once: for every block (tau, nu) of level k the host forms the column set
+// (level 0: the points of nu; k > 0: nu1_bar U nu2_bar, the skeletons of
+// (p_tau, nu1), (p_tau, nu2)) and the proxy rows (Eq. proxyv2v; tau itself at
+// k = L), the device evaluates all sampled blocks (entries.cu) and their
+// interpolative decompositions (cpqr.cu), and the skeletons come back to the
+// host for the next level.  K^L = K(tau_i, nu_bar) and the dense leaves are
+// evaluated straight into the factor arena.
+//
+// Apply plans.  Forward (Eq. butterfly_mat): step 0 = V^0 of every butterfly
+// and the dense leaves (y = D x); step t = W^t of the butterflies with L >= t
+// and K^L (y += ...) of those with L = t - 1.  Adjoint (reverse order,
+// conjugate transposes): step 0 = K^L^H and D^H; step u = W^{L-u+1}^H; step
+// L + 1 = V^0^H (y += ...).  Each butterfly's V^0^H lands in its own step,
+// so outputs of one step never overlap and the sum order is fixed.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <vector>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#include "hb_internal.cuh"
+
+namespace hb {
+
+struct BlockRec {
+  int rank = 0;
+  int ncols = 0;
+  long long f_off = -1;
+  long long xh_off = -1;
+  std::vector<long long> skel;   // tree positions, pivot order
+};
+
+struct Butterfly {
+  int l, oi, si, L;
+  std::vector<std::vector<BlockRec>> lev;   // lev[k][i * 2^(L-k) + j]
+  std::vector<long long> kl_off;            // K^L factor offset per leaf i of T_o
+};
+
+struct Job {
+  int bf, k, i, j;
+  std::vector<long long> rows, cols;        // tree positions
+};
+
+namespace {
+
+struct Segment {
+  double2* ptr;
+  long long count;
+  long long global_off;
+};
+
+long long node_lo(const hb_ctx* c, int level, long long idx) { return c->bounds[level][idx]; }
+long long node_hi(const hb_ctx* c, int level, long long idx) { return c->bounds[level][idx + 1]; }
+
+void form_job(const hb_ctx* c, const std::vector<Butterfly>& bfs, Job& jb, std::vector<int>& stamp,
+              int stamp_id) {
+  const Butterfly& b = bfs[jb.bf];
+  const int k = jb.k, L = b.L;
+  const long long t0 = node_lo(c, b.l + k, ((long long)b.oi << k) + jb.i);
+  const long long t1 = node_hi(c, b.l + k, ((long long)b.oi << k) + jb.i);
+  jb.cols.clear();
+  if (k == 0) {
+    const long long n0 = node_lo(c, b.l + L, ((long long)b.si << L) + jb.j);
+    const long long n1 = node_hi(c, b.l + L, ((long long)b.si << L) + jb.j);
+    for (long long p = n0; p < n1; ++p) jb.cols.push_back(p);
+  } else {
+    const long long w = 1LL << (L - k + 1);
+    const BlockRec& a = b.lev[k - 1][(jb.i / 2) * w + 2 * jb.j];
+    const BlockRec& bb = b.lev[k - 1][(jb.i / 2) * w + 2 * jb.j + 1];
+    jb.cols.insert(jb.cols.end(), a.skel.begin(), a.skel.end());
+    jb.cols.insert(jb.cols.end(), bb.skel.begin(), bb.skel.end());
+  }
+  if (k == L) {
+    jb.rows.resize((size_t)(t1 - t0));
+    for (long long p = t0; p < t1; ++p) jb.rows[p - t0] = p;
+  } else {
+    proxy_rows(c, t0, t1, jb.cols.data(), (int)jb.cols.size(), jb.rows, stamp, stamp_id);
+  }
+}
+
+}  // namespace
+
+void build(hb_ctx* c) {
+  const auto t_begin = std::chrono::steady_clock::now();
+  const int Lv = c->Lv;
+  cudaStream_t st = 0;
+  std::vector<Butterfly> bfs;
+  for (int l = 1; l <= Lv; ++l)
+    for (long long p = 0; p < (1LL << (l - 1)); ++p)
+      for (int d = 0; d < 2; ++d) {
+        Butterfly b;
+        b.l = l;
+        b.oi = (int)(2 * p + d);
+        b.si = (int)(2 * p + 1 - d);
+        b.L = Lv - l;
+        b.lev.assign(b.L + 1, std::vector<BlockRec>((size_t)1 << b.L));
+        bfs.push_back(std::move(b));
+      }
+
+  const long long ws_bytes = (long long)(c->opt.workspace_mb > 0 ? c->opt.workspace_mb : 2048) << 20;
+  const long long ws_elems = ws_bytes / (long long)sizeof(double2);
+  double2* d_A = dev_alloc<double2>((size_t)ws_elems);
+  std::vector<Segment> segs;
+  long long nfac = 0;
+  long long id_blocks = 0, sampled = 0;
+  int max_rank = 0;
+#ifdef _OPENMP
+  const int nthreads = omp_get_max_threads();
+#else
+  const int nthreads = 1;
+#endif
+  std::vector<std::vector<int>> stamps((size_t)nthreads, std::vector<int>((size_t)c->Nv, -1));
+  const int Lmax = Lv - 1;
+  int stamp_base = 0;
+
+  for (int k = 0; k <= Lmax; ++k) {
+    std::vector<Job> desc;
+    for (int bi = 0; bi < (int)bfs.size(); ++bi) {
+      const Butterfly& b = bfs[bi];
+      if (b.L < k) continue;
+      for (int i = 0; i < (1 << k); ++i)
+        for (int j = 0; j < (1 << (b.L - k)); ++j) desc.push_back(Job{bi, k, i, j, {}, {}});
+    }
+    const size_t JC = 8192;
+    for (size_t j0 = 0; j0 < desc.size(); j0 += JC) {
+      const size_t j1 = std::min(desc.size(), j0 + JC);
+#pragma omp parallel for schedule(dynamic, 16)
+      for (long long q = (long long)j0; q < (long long)j1; ++q) {
+#ifdef _OPENMP
+        const int tid = omp_get_thread_num();
+#else
+        const int tid = 0;
+#endif
+        form_job(c, bfs, desc[q], stamps[tid], stamp_base + (int)(q - j0) + 1);
+      }
+      stamp_base += (int)(j1 - j0) + 1;
+      if (stamp_base > (1 << 30)) {
+        for (auto& s : stamps) std::fill(s.begin(), s.end(), -1);
+        stamp_base = 0;
+      }
+      // workspace chunks
+      size_t q0 = j0;
+      while (q0 < j1) {
+        size_t q1 = q0;
+        long long used = 0;
+        while (q1 < j1) {
+          long long e = (long long)desc[q1].rows.size() * (long long)desc[q1].cols.size();
+          if (q1 > q0 && used + e > ws_elems) break;
+          if (e > ws_elems) throw Error{HB_ERR_OOM, "sampled block exceeds the build workspace"};
+          used += e;
+          ++q1;
+        }
+        const int cnt = (int)(q1 - q0);
+        BlockBatchHost B;
+        std::vector<int> hm(cnt), hn(cnt);
+        std::vector<long long> haoff(cnt), hsoff(cnt);
+        long long aoff = 0, soff = 0;
+        int max_n = 1;
+        for (int t = 0; t < cnt; ++t) {
+          Job& jb = desc[q0 + t];
+          std::vector<long long> rn(jb.rows.size()), cn(jb.cols.size());
+          for (size_t a = 0; a < rn.size(); ++a) rn[a] = c->perm[jb.rows[a]];
+          for (size_t a = 0; a < cn.size(); ++a) cn[a] = c->perm[jb.cols[a]];
+          add_block(B, c, rn.data(), (long long)rn.size(), cn.data(), (long long)cn.size(), aoff);
+          hm[t] = (int)rn.size();
+          hn[t] = (int)cn.size();
+          haoff[t] = aoff;
+          hsoff[t] = soff;
+          aoff += (long long)hm[t] * hn[t];
+          soff += hn[t];
+          max_n = std::max(max_n, hn[t]);
+        }
+        sampled += aoff;
+        id_blocks += cnt;
+        run_blocks(c, B, d_A, st);
+        int* d_m = upload(hm);
+        int* d_n = upload(hn);
+        long long* d_aoff = upload(haoff);
+        long long* d_soff = upload(hsoff);
+        int* d_rank = dev_alloc<int>(cnt);
+        int* d_perm = dev_alloc<int>((size_t)soff);
+        id_batch(cnt, d_m, d_n, d_aoff, d_A, c->opt.eps, d_rank, d_perm, d_soff, max_n, st);
+        std::vector<int> hrank(cnt), hperm((size_t)soff);
+        HB_CUDA(cudaMemcpyAsync(hrank.data(), d_rank, sizeof(int) * cnt, cudaMemcpyDeviceToHost, st));
+        HB_CUDA(cudaMemcpyAsync(hperm.data(), d_perm, sizeof(int) * soff, cudaMemcpyDeviceToHost, st));
+        HB_CUDA(cudaStreamSynchronize(st));
+        std::vector<long long> hvoff(cnt);
+        long long vacc = 0;
+        for (int t = 0; t < cnt; ++t) {
+          Job& jb = desc[q0 + t];
+          Butterfly& b = bfs[jb.bf];
+          BlockRec& br = b.lev[jb.k][(size_t)jb.i * (1u << (b.L - jb.k)) + jb.j];
+          const int r = hrank[t];
+          br.rank = r;
+          br.ncols = hn[t];
+          br.f_off = nfac + vacc;
+          br.skel.resize(r);
+          for (int a = 0; a < r; ++a) br.skel[a] = jb.cols[hperm[hsoff[t] + a]];
+          hvoff[t] = vacc;
+          vacc += (long long)r * hn[t];
+          max_rank = std::max(max_rank, r);
+        }
+        double2* seg = dev_alloc<double2>((size_t)vacc);
+        long long* d_voff = upload(hvoff);
+        emit_v(cnt, d_m, d_n, d_aoff, d_A, d_rank, d_perm, d_soff, d_voff, 1, seg, nullptr, st);
+        HB_CUDA(cudaStreamSynchronize(st));
+        segs.push_back(Segment{seg, vacc, nfac});
+        nfac += vacc;
+        for (void* p : {(void*)d_m, (void*)d_n, (void*)d_aoff, (void*)d_soff, (void*)d_rank, (void*)d_perm,
+                        (void*)d_voff})
+          dev_free(p);
+        for (int t = 0; t < cnt; ++t) {
+          std::vector<long long>().swap(desc[q0 + t].rows);
+        }
+        q0 = q1;
+      }
+    }
+  }
+
+  // K^L blocks and dense leaves, evaluated straight into factor segments
+  struct EJob {
+    std::vector<long long> rows, cols;   // natural indices
+    long long* target;
+  };
+  std::vector<EJob> ejobs;
+  for (auto& b : bfs) {
+    b.kl_off.assign((size_t)1 << b.L, -1);
+    for (long long i = 0; i < (1LL << b.L); ++i) {
+      const long long t0 = node_lo(c, b.l + b.L, ((long long)b.oi << b.L) + i);
+      const long long t1 = node_hi(c, b.l + b.L, ((long long)b.oi << b.L) + i);
+      EJob e;
+      for (long long p = t0; p < t1; ++p) e.rows.push_back(c->perm[p]);
+      for (long long p : b.lev[b.L][(size_t)i].skel) e.cols.push_back(c->perm[p]);
+      e.target = &b.kl_off[(size_t)i];
+      ejobs.push_back(std::move(e));
+    }
+  }
+  std::vector<long long> leaf_off((size_t)1 << Lv, -1);
+  for (long long t = 0; t < (1LL << Lv); ++t) {
+    EJob e;
+    for (long long p = node_lo(c, Lv, t); p < node_hi(c, Lv, t); ++p) e.rows.push_back(c->perm[p]);
+    e.cols = e.rows;
+    e.target = &leaf_off[(size_t)t];
+    ejobs.push_back(std::move(e));
+  }
+  {
+    size_t q0 = 0;
+    while (q0 < ejobs.size()) {
+      size_t q1 = q0;
+      long long used = 0;
+      while (q1 < ejobs.size()) {
+        long long e = (long long)ejobs[q1].rows.size() * (long long)ejobs[q1].cols.size();
+        if (q1 > q0 && used + e > ws_elems) break;
+        used += e;
+        ++q1;
+      }
+      BlockBatchHost B;
+      long long off = 0;
+      for (size_t q = q0; q < q1; ++q) {
+        EJob& e = ejobs[q];
+        add_block(B, c, e.rows.data(), (long long)e.rows.size(), e.cols.data(), (long long)e.cols.size(), off);
+        *e.target = nfac + off;
+        off += (long long)e.rows.size() * (long long)e.cols.size();
+      }
+      double2* seg = dev_alloc<double2>((size_t)off);
+      run_blocks(c, B, seg, st);
+      segs.push_back(Segment{seg, off, nfac});
+      nfac += off;
+      sampled += off;
+      q0 = q1;
+    }
+  }
+  dev_free(d_A);
+
+  // pack the arenas
+  c->n_factor = nfac;
+  c->d_f64 = dev_alloc<double2>((size_t)nfac);
+  for (const Segment& s : segs) {
+    if (s.count) HB_CUDA(cudaMemcpyAsync(c->d_f64 + s.global_off, s.ptr, sizeof(double2) * s.count,
+                                         cudaMemcpyDeviceToDevice, st));
+  }
+  HB_CUDA(cudaStreamSynchronize(st));
+  for (const Segment& s : segs) dev_free(s.ptr);
+  c->d_f32 = dev_alloc<float2>((size_t)nfac);
+  convert_f64_f32(c->d_f64, c->d_f32, nfac, st);
+  HB_CUDA(cudaStreamSynchronize(st));
+
+  // xh offsets
+  long long xh = 0;
+  for (auto& b : bfs)
+    for (int k = 0; k <= b.L; ++k)
+      for (auto& br : b.lev[k]) {
+        br.xh_off = xh;
+        xh += br.rank;
+      }
+  c->xh_rows = xh;
+
+  // task plans
+  for (int dir = 0; dir < 2; ++dir) {
+    std::vector<std::vector<Task>> steps((size_t)Lv + 1);
+    auto mk = [](long long y_off, int r_out, unsigned char y_buf, unsigned char acc) {
+      Task t{};
+      t.y_off = y_off;
+      t.r_out = r_out;
+      t.y_buf = y_buf;
+      t.accumulate = acc;
+      t.nterm = 1;
+      return t;
+    };
+    for (long long t = 0; t < (1LL << Lv); ++t) {
+      const long long p0 = node_lo(c, Lv, t);
+      const int sz = (int)(node_hi(c, Lv, t) - p0);
+      Task tk = mk(p0, sz, 1, 0);
+      tk.f_off[0] = leaf_off[(size_t)t];
+      tk.x_off[0] = p0;
+      tk.r_in[0] = sz;
+      tk.x_buf = 0;
+      tk.conj_t = (unsigned char)dir;
+      tk.kind = 0;
+      steps[0].push_back(tk);
+    }
+    for (auto& b : bfs) {
+      const int L = b.L;
+      for (int k = 0; k <= L + 1; ++k) {
+        if (dir == 0) {
+          if (k == 0) {
+            for (int j = 0; j < (1 << L); ++j) {
+              const BlockRec& br = b.lev[0][(size_t)j];
+              const long long n0 = node_lo(c, b.l + L, ((long long)b.si << L) + j);
+              const int nn = (int)(node_hi(c, b.l + L, ((long long)b.si << L) + j) - n0);
+              Task tk = mk(br.xh_off, br.rank, 2, 0);
+              tk.f_off[0] = br.f_off;
+              tk.x_buf = 0;
+              tk.x_off[0] = n0;
+              tk.r_in[0] = nn;
+              tk.kind = 1;
+              steps[0].push_back(tk);
+            }
+          } else if (k <= L) {
+            const int w = 1 << (L - k);
+            for (int i = 0; i < (1 << k); ++i)
+              for (int j = 0; j < w; ++j) {
+                const BlockRec& br = b.lev[k][(size_t)i * w + j];
+                const BlockRec& c1 = b.lev[k - 1][(size_t)(i / 2) * (2 * w) + 2 * j];
+                const BlockRec& c2 = b.lev[k - 1][(size_t)(i / 2) * (2 * w) + 2 * j + 1];
+                Task tk = mk(br.xh_off, br.rank, 2, 0);
+                tk.f_off[0] = br.f_off;
+                tk.x_buf = 2;
+                tk.x_off[0] = c1.xh_off;
+                tk.r_in[0] = c1.rank + c2.rank;
+                tk.kind = 2;
+                steps[k].push_back(tk);
+              }
+          } else {
+            for (int i = 0; i < (1 << L); ++i) {
+              const BlockRec& br = b.lev[L][(size_t)i];
+              const long long t0 = node_lo(c, b.l + L, ((long long)b.oi << L) + i);
+              const int sz = (int)(node_hi(c, b.l + L, ((long long)b.oi << L) + i) - t0);
+              Task tk = mk(t0, sz, 1, 1);
+              tk.f_off[0] = b.kl_off[(size_t)i];
+              tk.x_buf = 2;
+              tk.x_off[0] = br.xh_off;
+              tk.r_in[0] = br.rank;
+              tk.kind = 3;
+              steps[L + 1].push_back(tk);
+            }
+          }
+        } else {
+          if (k == 0) {
+            for (int i = 0; i < (1 << L); ++i) {
+              const BlockRec& br = b.lev[L][(size_t)i];
+              const long long t0 = node_lo(c, b.l + L, ((long long)b.oi << L) + i);
+              const int sz = (int)(node_hi(c, b.l + L, ((long long)b.oi << L) + i) - t0);
+              Task tk = mk(br.xh_off, br.rank, 2, 0);
+              tk.f_off[0] = b.kl_off[(size_t)i];
+              tk.x_buf = 0;
+              tk.x_off[0] = t0;
+              tk.r_in[0] = sz;
+              tk.conj_t = 1;
+              tk.kind = 3;
+              steps[0].push_back(tk);
+            }
+          } else if (k <= L) {
+            const int t = L - k + 1;            // adjoint of W^t
+            const int w = 1 << (L - t);
+            for (int p = 0; p < (1 << (t - 1)); ++p)
+              for (int j = 0; j < w; ++j) {
+                const BlockRec& o1 = b.lev[t - 1][(size_t)p * (2 * w) + 2 * j];
+                const BlockRec& o2 = b.lev[t - 1][(size_t)p * (2 * w) + 2 * j + 1];
+                Task tk = mk(o1.xh_off, o1.rank + o2.rank, 2, 0);
+                tk.nterm = 2;
+                for (int cc = 0; cc < 2; ++cc) {
+                  const BlockRec& br = b.lev[t][(size_t)(2 * p + cc) * w + j];
+                  tk.f_off[cc] = br.f_off;
+                  tk.x_off[cc] = br.xh_off;
+                  tk.r_in[cc] = br.rank;
+                }
+                tk.x_buf = 2;
+                tk.conj_t = 1;
+                tk.kind = 2;
+                steps[k].push_back(tk);
+              }
+          } else {
+            for (int j = 0; j < (1 << L); ++j) {
+              const BlockRec& br = b.lev[0][(size_t)j];
+              const long long n0 = node_lo(c, b.l + L, ((long long)b.si << L) + j);
+              const int nn = (int)(node_hi(c, b.l + L, ((long long)b.si << L) + j) - n0);
+              Task tk = mk(n0, nn, 1, 1);
+              tk.f_off[0] = br.f_off;
+              tk.x_buf = 2;
+              tk.x_off[0] = br.xh_off;
+              tk.r_in[0] = br.rank;
+              tk.conj_t = 1;
+              tk.kind = 1;
+              steps[L + 1].push_back(tk);
+            }
+          }
+        }
+      }
+    }
+    c->tasks_h[dir].clear();
+    std::vector<int> begins;
+    for (auto& s : steps) {
+      begins.push_back((int)c->tasks_h[dir].size());
+      c->tasks_h[dir].insert(c->tasks_h[dir].end(), s.begin(), s.end());
+    }
+    begins.push_back((int)c->tasks_h[dir].size());
+    c->step_begin[dir] = begins;
+    c->d_tasks[dir] = upload(c->tasks_h[dir]);
+  }
+  HB_CUDA(cudaDeviceSynchronize());
+
+  c->max_rank = max_rank;
+  c->stats.max_rank = max_rank;
+  c->stats.factor_entries = nfac;
+  c->stats.factor_bytes_fp64 = nfac * (long long)sizeof(double2);
+  c->stats.factor_bytes_mixed = nfac * (long long)sizeof(float2);
+  c->stats.id_blocks = id_blocks;
+  c->stats.sampled_entries = sampled;
+  c->stats.skeleton_rows = c->xh_rows;
+  int launches = 2;
+  for (size_t s = 0; s + 1 < c->step_begin[0].size(); ++s)
+    if (c->step_begin[0][s + 1] > c->step_begin[0][s]) ++launches;
+  c->stats.apply_launches = launches;
+  c->stats.build_ms =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_begin).count();
+}
+
+}  // namespace hb

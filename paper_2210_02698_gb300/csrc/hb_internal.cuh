@@ -1,0 +1,184 @@
+// hb_internal.cuh - handle layout and helpers shared by the library's
+// translation units (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/hb.h"
+
+namespace hb {
+
+// ------------------------------------------------------------- errors ----
+struct Error {
+  hb_status code;
+  std::string msg;
+};
+
+#define HB_CUDA(call)                                                          \
+  do {                                                                         \
+    cudaError_t e_ = (call);                                                   \
+    if (e_ != cudaSuccess) {                                                   \
+      throw ::hb::Error{HB_ERR_CUDA, std::string(#call) + ": " +              \
+                                         cudaGetErrorString(e_)};              \
+    }                                                                          \
+  } while (0)
+
+#define HB_CHECK_LAUNCH() HB_CUDA(cudaGetLastError())
+
+inline Error arg_error(const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  return Error{HB_ERR_ARG, buf};
+}
+
+// Device allocation that reports HB_ERR_OOM.
+template <class T>
+T* dev_alloc(size_t count) {
+  if (count == 0) count = 1;
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw Error{e == cudaErrorMemoryAllocation ? HB_ERR_OOM : HB_ERR_CUDA,
+                std::string("cudaMalloc(") + std::to_string(count * sizeof(T)) +
+                    " bytes): " + cudaGetErrorString(e)};
+  }
+  return static_cast<T*>(p);
+}
+
+inline void dev_free(void* p) {
+  if (p) cudaFree(p);
+}
+
+template <class T>
+T* upload(const std::vector<T>& v, cudaStream_t st = 0) {
+  T* d = dev_alloc<T>(v.size());
+  if (!v.empty()) HB_CUDA(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+  return d;
+}
+
+// ------------------------------------------------------ entry context ----
+// Everything a kernel needs to evaluate K_ij (passed by value).
+struct EntryParams {
+  int nx, ny, nI;
+  int NI;
+  double omega;
+  const double* LX;      // nx x nI   l_k(x_a)
+  const double* LZ;      // ny x nI   l_k(z_b)
+  const double* H;       // 3 x ny x NI x nI  (see entries.cu)
+  const double2* self;   // Nv self terms K_ii
+};
+
+// ------------------------------------------------------ butterfly plan ----
+// One step task: Y (r_out x R) (=|+=) sum_{t < nterm} op_t(F_t) X_t, with
+// op(F) = F (F stored column-major r_out x r_in, ld = r_out) or, when
+// conj_t, op(F) = F^H (F stored column-major r_in x r_out, ld = r_in).
+// Vector buffers are row-major with the R right-hand sides contiguous:
+// buffer 0 = x (tree-ordered input), 1 = y (tree-ordered output), 2 = xh
+// (all butterfly intermediate vectors).
+struct Task {
+  long long y_off;
+  long long f_off[2];
+  long long x_off[2];
+  int r_out;
+  int r_in[2];
+  unsigned char nterm, x_buf, y_buf, accumulate;
+  unsigned char conj_t, kind, pad0, pad1;
+};
+
+// Host-side batch of ragged entry blocks (entries.cu).
+struct BlockMeta {
+  long long row_off, m, col_off, n, out_off, seg_off, nseg, pad;
+};
+struct BlockBatchHost {
+  std::vector<BlockMeta> meta;
+  std::vector<long long> rows, cols, segs, items;
+  std::vector<int> rdst;
+};
+
+}  // namespace hb
+
+struct hb_ctx {
+  // problem
+  int nx = 0, ny = 0;
+  long long Nv = 0;
+  double x0 = 0, y0 = 0, h = 0, omega = 0;
+  int nI = 0, NI = 0;
+  hb_options opt{};
+  std::string err;
+  std::vector<double> nodes_x, nodes_y, n_cells;
+  std::vector<double> tab[3];  // tau2, v0, v1 row-major NI x NI
+
+  // device: interpolation and self terms
+  double* d_nodes = nullptr;   // nodes_x then nodes_y
+  double* d_tab = nullptr;     // 3 x NI x NI (forward), then 3 x NI x NI transposed
+  double* d_LX = nullptr;
+  double* d_LZ = nullptr;
+  double* d_H[2] = {nullptr, nullptr};
+  double* d_ncell = nullptr;
+  double2* d_self = nullptr;
+
+  // cluster tree
+  int Lv = 0;
+  std::vector<long long> perm;               // tree position -> natural index
+  std::vector<long long> iperm;              // natural index -> tree position
+  std::vector<std::vector<long long>> bounds;
+  long long* d_perm = nullptr;
+
+  // build results
+  bool built = false;
+  hb_stats stats{};
+  // factor arenas: FP64 (double2) and mixed (float2), same element offsets
+  long long n_factor = 0;
+  double2* d_f64 = nullptr;
+  float2* d_f32 = nullptr;
+  // apply plans: steps[0] forward, steps[1] adjoint; each step = task range
+  std::vector<int> step_begin[2];
+  std::vector<hb::Task> tasks_h[2];
+  hb::Task* d_tasks[2] = {nullptr, nullptr};
+  long long xh_rows = 0;
+  int max_rank = 0;
+
+  // apply scratch (sized for cap_rhs right-hand sides)
+  int cap_rhs = 0;
+  void* d_x = nullptr;
+  void* d_y = nullptr;
+  void* d_xh = nullptr;
+
+  // timing
+  bool timing = false;
+  std::vector<std::string> tnames;
+  std::vector<double> tms;
+  std::vector<long long> tcount;
+};
+
+namespace hb {
+hb::EntryParams entry_params(const hb_ctx* c, int transposed);
+void setup_tables(hb_ctx* c);                 // entries.cu
+void dense_apply(hb_ctx* c, const double2* s, double2* u, int nrhs, int adjoint, cudaStream_t st);
+void eval_entries(hb_ctx* c, const long long* rows, int m, const long long* cols, int n,
+                  double2* out, cudaStream_t st);
+void add_block(BlockBatchHost& B, const hb_ctx* c, const long long* rows, long long m,
+               const long long* cols, long long n, long long out_off);
+void run_blocks(hb_ctx* c, BlockBatchHost& B, double2* d_out, cudaStream_t st);
+void id_batch(int count, const int* d_m, const int* d_n, const long long* d_aoff, double2* d_A,
+              double eps, int* d_rank, int* d_perm, const long long* d_soff, int max_n, cudaStream_t st);
+void emit_v(int count, const int* d_m, const int* d_n, const long long* d_aoff, const double2* d_A,
+            const int* d_rank, const int* d_perm, const long long* d_soff, const long long* d_voff,
+            int ld_is_rank, double2* V64, float2* V32, cudaStream_t st);
+void build(hb_ctx* c);
+void convert_f64_f32(const double2* a, float2* b, long long n, cudaStream_t st);
+void apply_bf(hb_ctx* c, const double2* s, double2* u, int nrhs, int adjoint, int precision,
+              cudaStream_t st);
+void tree_build(hb_ctx* c);
+void proxy_rows(const hb_ctx* c, long long t0, long long t1, const long long* seeds, int nseeds,
+                std::vector<long long>& out, std::vector<int>& stamp, int stamp_id);
+}  // namespace hb

@@ -1,0 +1,106 @@
+"""GPU HODBF / butterfly construction and apply (Sec. 4.2, Eq. butterfly_mat)
+against the oracle.  Bars: tree order and proxy rows bit-exact; FP64
+butterfly at eps = 1e-6 within rel-L2 1e-5 of the dense oracle; mixed
+precision within 1e-4; adjoint identity to rounding."""
+import numpy as np
+import pytest
+
+from tests._common import from_dev, gpu_op, oracle_op, rel_l2, to_dev
+from paper_2210_02698_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2210_02698_gb300 import build
+    build.build()
+
+
+def _apply(op, s, adjoint=False):
+    import torch
+    nrhs = s.shape[1]
+    out = torch.empty((nrhs, s.shape[0]), dtype=torch.complex128, device="cuda")
+    (op.apply_adjoint if adjoint else op.apply)(to_dev(s), out, nrhs)
+    torch.cuda.synchronize()
+    return from_dev(out)
+
+
+@pytest.mark.parametrize("N,leaf", [(32, 64), (24, 20), (64, 64)])
+def test_tree_and_proxy_rows_match_oracle(N, leaf):
+    from oracle import tree
+    w = W.small_workload(W.GRADIENT, N, N / 8, 1, leaf=leaf)
+    gp = gpu_op(w)
+    perm, bounds = tree.cluster_tree(N, leaf)
+    assert np.array_equal(gp.tree_perm(), perm)
+    rng = np.random.default_rng(N)
+    for lvl in range(1, len(bounds)):
+        k = rng.integers(0, (1 << lvl) - 1)
+        t0, t1 = int(bounds[lvl][k]), int(bounds[lvl][k + 1])
+        s0, s1 = int(bounds[lvl][k + 1]), int(bounds[lvl][k + 2])
+        seeds = rng.choice(np.arange(s0, s1), size=min(s1 - s0, 7), replace=False)
+        want = tree.proxy_rows(t0, t1, seeds, w.chi, 10.0, perm, N)
+        assert np.array_equal(gp.proxy_rows(t0, t1, seeds), want)
+
+
+@pytest.mark.parametrize("N,leaf,nrhs", [(32, 64, 3), (48, 32, 2), (64, 64, 4)])
+def test_butterfly_fp64_and_mixed_vs_dense_oracle(N, leaf, nrhs):
+    from oracle import dense
+    from paper_2210_02698_gb300 import binding
+    w = W.small_workload(W.GRADIENT, N, N / 8, nrhs, leaf=leaf)
+    og, gp = oracle_op(w), gpu_op(w, precision=binding.HB_FP64)
+    gp.build()
+    s = W.complex_normal_sources(w.grid.Nv, nrhs, 41)
+    want = dense.apply(og, s)
+    got = _apply(gp, s)
+    assert rel_l2(got, want) < 1e-5
+    gp.set_precision(binding.HB_MIXED_BF16X3)
+    assert rel_l2(_apply(gp, s), want) < 1e-4
+    # adjoint against the dense oracle adjoint, both precisions
+    gp.set_precision(binding.HB_FP64)
+    wantA = dense.adjoint(og, s)
+    assert rel_l2(_apply(gp, s, adjoint=True), wantA) < 1e-5
+    gp.set_precision(binding.HB_MIXED_BF16X3)
+    assert rel_l2(_apply(gp, s, adjoint=True), wantA) < 1e-4
+
+
+def test_fp64_adjoint_is_exact_adjoint_of_compressed_operator():
+    from paper_2210_02698_gb300 import binding
+    w = W.small_workload(W.GRADIENT, 64, 8, 2)
+    gp = gpu_op(w, precision=binding.HB_FP64)
+    gp.build()
+    x = W.complex_normal_sources(w.grid.Nv, 2, 1)
+    y = W.complex_normal_sources(w.grid.Nv, 2, 2)
+    Ax = _apply(gp, x)
+    AHy = _apply(gp, y, adjoint=True)
+    lhs = np.vdot(y, Ax)
+    rhs = np.vdot(AHy, x)
+    assert abs(lhs - rhs) <= 1e-13 * np.linalg.norm(Ax) * np.linalg.norm(y)
+
+
+def test_tight_tolerance_reproduces_dense():
+    from oracle import dense
+    from paper_2210_02698_gb300 import binding
+    w = W.small_workload(W.GRADIENT, 32, 4, 1, eps=1e-13)
+    og, gp = oracle_op(w), gpu_op(w, precision=binding.HB_FP64)
+    gp.build()
+    s = W.complex_normal_sources(w.grid.Nv, 1, 9)
+    assert rel_l2(_apply(gp, s), dense.apply(og, s)) < 1e-11
+
+
+def test_grad256_fullsize_sampled_rows():
+    """The 256^2, 16-RHS workload in the configuration the benchmark times."""
+    from oracle import dense
+    from paper_2210_02698_gb300 import binding
+    w = W.WORKLOADS["grad256"]
+    og, gp = oracle_op(w), gpu_op(w, precision=binding.HB_FP64)
+    gp.build()
+    s = W.workload_sources(w)
+    rows = W.sample_rows(w.grid.Nv, 24, 99)
+    want = dense.apply(og, s, rows=rows, chunk=8192)
+    assert rel_l2(_apply(gp, s)[rows], want) < 1e-5
+    gp.set_precision(binding.HB_MIXED_BF16X3)
+    assert rel_l2(_apply(gp, s)[rows], want) < 1e-4

@@ -1,0 +1,66 @@
+"""CPU checks of the C-ABI library: it builds for sm_103a, loads, exports
+every symbol include/hb.h declares, and rejects bad arguments without a GPU."""
+import ctypes as C
+import shutil
+
+import numpy as np
+import pytest
+
+from tests._common import header_symbols
+
+
+@pytest.fixture(scope="module")
+def L():
+    if shutil.which("nvcc") is None and not __import__("os").path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    from paper_2210_02698_gb300 import binding, build
+    build.build()
+    return binding.lib()
+
+
+def test_every_declared_symbol_is_exported(L):
+    from paper_2210_02698_gb300 import binding
+    syms = header_symbols()
+    assert set(syms) == set(binding.EXPORTS)
+    for s in syms:
+        assert hasattr(L, s), s
+
+
+def test_argument_errors_without_compute(L):
+    from paper_2210_02698_gb300 import binding
+    hnd = C.c_void_p()
+    # null arguments -> HB_ERR_ARG, message kept per thread
+    assert L.hb_create(None, None, 1.0, None, C.byref(hnd)) == binding.HB_ERR_ARG
+    assert b"null" in L.hb_last_error(None)
+    g = binding.Grid(4, 4, 0.0, 0.0, 0.25)
+    nodes = np.linspace(0.1, 0.9, 3)
+    tab = np.zeros((9, 9))
+    nc = np.ones(16)
+    t = binding.Tables(3, nodes.ctypes.data, nodes.ctypes.data, tab.ctypes.data, tab.ctypes.data,
+                       tab.ctypes.data, nc.ctypes.data)
+    o = binding.Options(1e-6, 4, 20.0, 10.0, 0, 0, 0)
+    assert L.hb_create(C.byref(g), C.byref(t), -1.0, C.byref(o), C.byref(hnd)) == binding.HB_ERR_ARG
+    bad = binding.Options(0.0, 4, 20.0, 10.0, 0, 0, 0)
+    assert L.hb_create(C.byref(g), C.byref(t), 5.0, C.byref(bad), C.byref(hnd)) == binding.HB_ERR_ARG
+    t17 = binding.Tables(17, nodes.ctypes.data, nodes.ctypes.data, tab.ctypes.data, tab.ctypes.data,
+                         tab.ctypes.data, nc.ctypes.data)
+    assert L.hb_create(C.byref(g), C.byref(t17), 5.0, C.byref(o), C.byref(hnd)) == binding.HB_ERR_UNSUPPORTED
+    assert L.hb_apply(None, None, None, 1, None) == binding.HB_ERR_ARG
+    assert L.hb_id_batch(-1, None, None, None, None, 1e-6, None, None, None) == binding.HB_ERR_ARG
+    L.hb_destroy(None)
+
+
+def test_no_device_is_an_error_not_a_fallback(L):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2210_02698_gb300 import binding
+    g = binding.Grid(4, 4, 0.0, 0.0, 0.25)
+    nodes = np.linspace(0.1, 0.9, 3)
+    tab = np.zeros((9, 9))
+    nc = np.ones(16)
+    t = binding.Tables(3, nodes.ctypes.data, nodes.ctypes.data, tab.ctypes.data, tab.ctypes.data,
+                       tab.ctypes.data, nc.ctypes.data)
+    o = binding.Options(1e-6, 4, 20.0, 10.0, 0, 0, 0)
+    hnd = C.c_void_p()
+    assert L.hb_create(C.byref(g), C.byref(t), 5.0, C.byref(o), C.byref(hnd)) == binding.HB_ERR_CUDA
