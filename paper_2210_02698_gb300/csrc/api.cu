@@ -40,6 +40,8 @@ void free_all(hb_ctx* c) {
   hb::dev_free(c->d_xh);
   hb::dev_free(c->d_tasks[0]);
   hb::dev_free(c->d_tasks[1]);
+  hb::dev_free(c->d_units[0]);
+  hb::dev_free(c->d_units[1]);
 }
 
 void check_vec_args(hb_ctx* c, const void* a, const void* b, int nrhs) {

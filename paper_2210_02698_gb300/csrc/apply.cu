@@ -206,7 +206,14 @@ void apply_bf(hb_ctx* c, const double2* s, double2* u, int nrhs, int adjoint, in
     gather_kernel<float2><<<grid, 256, 0, st>>>(s, c->d_perm, (float2*)c->d_x, c->Nv, nrhs, scale);
     HB_CHECK_LAUNCH();
     ts.end();
-    run_steps<float2>(c, c->d_f32, nrhs, adjoint, st, ts);
+    const std::vector<int>& su = c->step_units[adjoint];
+    for (size_t k = 0; k + 1 < su.size(); ++k) {
+      if (su[k + 1] == su[k]) continue;
+      ts.begin(adjoint ? "bf_step_mma_adjoint" : "bf_step_mma");
+      mma_step_launch(c->d_units[adjoint], su[k], su[k + 1], c->d_tasks[adjoint], c->d_f32, (float2*)c->d_x,
+                      (float2*)c->d_y, (float2*)c->d_xh, nrhs, st);
+      ts.end();
+    }
     ts.begin("scatter");
     scatter_kernel<float2><<<grid, 256, 0, st>>>((float2*)c->d_y, c->d_perm, u, c->Nv, nrhs);
     HB_CHECK_LAUNCH();

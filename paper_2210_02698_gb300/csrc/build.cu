@@ -440,6 +440,7 @@ void build(hb_ctx* c) {
     begins.push_back((int)c->tasks_h[dir].size());
     c->step_begin[dir] = begins;
     c->d_tasks[dir] = upload(c->tasks_h[dir]);
+    mma_plan_build(c, dir, c->step_units[dir], &c->d_units[dir]);
   }
   HB_CUDA(cudaDeviceSynchronize());
 

@@ -144,6 +144,8 @@ struct hb_ctx {
   std::vector<int> step_begin[2];
   std::vector<hb::Task> tasks_h[2];
   hb::Task* d_tasks[2] = {nullptr, nullptr};
+  std::vector<int> step_units[2];          // warp-unit ranges of the tensor-core steps
+  void* d_units[2] = {nullptr, nullptr};
   long long xh_rows = 0;
   int max_rank = 0;
 
@@ -176,6 +178,9 @@ void emit_v(int count, const int* d_m, const int* d_n, const long long* d_aoff, 
             int ld_is_rank, double2* V64, float2* V32, cudaStream_t st);
 void build(hb_ctx* c);
 void convert_f64_f32(const double2* a, float2* b, long long n, cudaStream_t st);
+void mma_plan_build(hb_ctx* c, int dir, std::vector<int>& step_units, void** d_units_out);
+void mma_step_launch(const void* d_units, int u0, int u1, const Task* d_tasks, const float2* F, float2* x,
+                     float2* y, float2* xh, int R, cudaStream_t st);
 void apply_bf(hb_ctx* c, const double2* s, double2* u, int nrhs, int adjoint, int precision,
               cudaStream_t st);
 void tree_build(hb_ctx* c);

@@ -104,3 +104,38 @@ def test_grad256_fullsize_sampled_rows():
     assert rel_l2(_apply(gp, s)[rows], want) < 1e-5
     gp.set_precision(binding.HB_MIXED_BF16X3)
     assert rel_l2(_apply(gp, s)[rows], want) < 1e-4
+
+
+def test_autograd_gradient_matches_finite_differences():
+    """Source-inversion loss ||P u(s) - d||^2 with the hand-written adjoint as
+    backward; the loss is quadratic in s so central differences are exact up
+    to rounding (Sec. 3.1 operator, adjoint apply)."""
+    import torch
+    from paper_2210_02698_gb300 import binding
+    from paper_2210_02698_gb300.autograd import hb_apply
+    w = W.small_workload(W.GRADIENT, 64, 8, 1)
+    for prec, tol in ((binding.HB_FP64, 1e-8), (binding.HB_MIXED_BF16X3, 1e-4)):
+        gp = gpu_op(w, precision=prec)
+        gp.build()
+        rng = np.random.default_rng(12)
+        P = torch.from_numpy(np.sort(rng.choice(w.grid.Nv, 64, replace=False))).cuda()
+        s_ref = torch.from_numpy(W.complex_normal_sources(w.grid.Nv, 1, 3).T.copy()).cuda()
+        with torch.no_grad():
+            d = hb_apply(s_ref, gp)[:, P]
+        s0 = torch.from_numpy(W.complex_normal_sources(w.grid.Nv, 1, 4).T.copy()).cuda()
+        s = s0.clone().requires_grad_(True)
+
+        def loss(x):
+            r = hb_apply(x, gp)[:, P] - d
+            return (r.abs() ** 2).sum()
+
+        L = loss(s)
+        L.backward()
+        g = s.grad.detach()
+        for k in range(8):
+            dl = torch.from_numpy(W.complex_normal_sources(w.grid.Nv, 1, 100 + k).T.copy()).cuda()
+            t = 1e-3 * float(s0.norm() / dl.norm())
+            with torch.no_grad():
+                fd = (loss(s0 + t * dl) - loss(s0 - t * dl)) / (2 * t)
+            pred = torch.real(torch.vdot(g.reshape(-1), dl.reshape(-1)))
+            assert abs(float(fd - pred)) <= tol * abs(float(pred)) + tol * float(g.norm() * dl.norm())
