@@ -167,6 +167,31 @@ hb_status hb_entries(hb_handle h, const long long* rows, int m, const long long*
 hb_status hb_id_batch(int count, const int* m, const int* n, const long long* a_off,
                       void* A, double eps, int* rank, int* skel, void* V);
 
+/* hb_id_batch_noalloc: the decompositions of hb_id_batch, with the same
+ * arguments, layouts and results (skel receives the full pivot order of each
+ * matrix, its first rank[b] entries being the skeleton), for callers that
+ * cannot allocate device memory: code running under another framework's
+ * memory manager, which has reserved the device memory for its own pool (a
+ * raw cudaMalloc can then fail, or stall every stream with its implicit
+ * synchronisation), and latency-critical paths that must not take that
+ * synchronisation.  The paper has no counterpart: this is a library
+ * interface concern, not part of the method.
+ * It calls no cudaMalloc / cudaFree and no allocating library routine: the
+ * per-matrix sizes and offsets the kernels read on the device go to a 2 MiB
+ * static device array that every GPU loading the library keeps until the
+ * process exits.  Limit: count <= 65536 matrices (larger counts return
+ * HB_ERR_ARG with a message; nothing is launched).
+ * Asynchronous on `stream` (NULL = legacy default stream); the host arrays
+ * m, n, a_off may be reused on return.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) for that device: make
+ * that first call before any stream capture.  All calls share the array,
+ * whose contents after a call are that call's metadata; each call writes
+ * everything it reads, so nothing must start at zero, but calls that
+ * overlap on the GPU (other streams or host threads without a
+ * synchronisation in between) race on it. */
+hb_status hb_id_batch_noalloc(int count, const int* m, const int* n, const long long* a_off,
+                              void* A, double eps, int* rank, int* skel, void* V, void* stream);
+
 /* hb_tree_perm: copy the cluster-tree permutation (tree position ->
  * natural index, N_v int64) to a HOST array.  Valid after hb_create. */
 hb_status hb_tree_perm(hb_handle h, long long* perm_out);

@@ -22,7 +22,7 @@ STATUS = {0: "HB_OK", 1: "HB_ERR_ARG", 2: "HB_ERR_CUDA", 3: "HB_ERR_OOM", 4: "HB
 
 # every symbol include/hb.h declares
 EXPORTS = ["hb_create", "hb_build", "hb_apply", "hb_apply_adjoint", "hb_set_precision",
-           "hb_apply_dense", "hb_apply_dense_adjoint", "hb_entries", "hb_id_batch",
+           "hb_apply_dense", "hb_apply_dense_adjoint", "hb_entries", "hb_id_batch", "hb_id_batch_noalloc",
            "hb_tree_perm", "hb_proxy_rows", "hb_info", "hb_set_kernel_timing",
            "hb_kernel_times", "hb_last_error", "hb_destroy"]
 
@@ -70,6 +70,7 @@ def lib():
         L.hb_set_precision.argtypes = [vp, i]
         L.hb_entries.argtypes = [vp, vp, i, vp, i, vp, vp]
         L.hb_id_batch.argtypes = [i, vp, vp, vp, vp, d, vp, vp, vp]
+        L.hb_id_batch_noalloc.argtypes = [i, vp, vp, vp, vp, d, vp, vp, vp, vp]
         L.hb_tree_perm.argtypes = [vp, vp]
         L.hb_proxy_rows.argtypes = [vp, ll, ll, vp, i, vp, vp]
         L.hb_info.argtypes = [vp, C.POINTER(Stats)]
@@ -208,6 +209,15 @@ def id_batch(A, m, n, a_off, eps, rank, skel, V):
     a_off = np.ascontiguousarray(a_off, dtype=np.int64)
     _check(lib().hb_id_batch(len(m), m.ctypes.data, n.ctypes.data, a_off.ctypes.data, _ptr(A),
                              float(eps), _ptr(rank), _ptr(skel), _ptr(V)))
+
+
+def id_batch_noalloc(A, m, n, a_off, eps, rank, skel, V, stream=None):
+    """hb_id_batch_noalloc: hb_id_batch without any device allocation."""
+    m = np.ascontiguousarray(m, dtype=np.int32)
+    n = np.ascontiguousarray(n, dtype=np.int32)
+    a_off = np.ascontiguousarray(a_off, dtype=np.int64)
+    _check(lib().hb_id_batch_noalloc(len(m), m.ctypes.data, n.ctypes.data, a_off.ctypes.data, _ptr(A),
+                                     float(eps), _ptr(rank), _ptr(skel), _ptr(V), _stream_ptr(stream)))
 
 
 def load_tables(path):

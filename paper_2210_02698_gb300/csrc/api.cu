@@ -206,6 +206,16 @@ hb_status hb_id_batch(int count, const int* m, const int* n, const long long* a_
   });
 }
 
+hb_status hb_id_batch_noalloc(int count, const int* m, const int* n, const long long* a_off, void* A, double eps,
+                              int* rank, int* skel, void* V, void* stream) {
+  return guarded(nullptr, [&] {
+    if (count < 0 || (count > 0 && (!m || !n || !a_off || !A || !rank || !skel || !V)))
+      throw hb::arg_error("bad hb_id_batch_noalloc arguments");
+    if (!(eps >= 0)) throw hb::arg_error("eps must be >= 0");
+    hb::id_batch_noalloc(count, m, n, a_off, (double2*)A, eps, rank, skel, (double2*)V, (cudaStream_t)stream);
+  });
+}
+
 hb_status hb_tree_perm(hb_handle h, long long* perm_out) {
   return guarded(h, [&] {
     if (!h || !perm_out) throw hb::arg_error("null argument");

@@ -213,3 +213,115 @@ void emit_v(int count, const int* d_m, const int* d_n, const long long* d_aoff, 
 }
 
 }  // namespace hb
+
+// ---------------------------------------------------------------------------
+// hb_id_batch_noalloc: the same batched decompositions without allocating.
+//
+// Some callers cannot call cudaMalloc: code running under another
+// framework's memory manager (which has reserved the device memory for its
+// own pool, so a raw cudaMalloc can fail even though memory is free in that
+// pool, or would stall every stream with its implicit synchronisation), and
+// latency-critical paths that must not take that synchronisation.  For them
+// the per-matrix metadata the kernels read from device memory (sizes and
+// offsets) lives in this file-scope array instead of a fresh allocation.
+// Every GPU that loads the library holds the array until the process exits.
+// The pivot order goes straight into the caller's skel buffer, so nothing
+// else is needed.  Every call overwrites the metadata it reads, so nothing
+// has to start at zero; calls that overlap on the GPU (different streams or
+// host threads without a synchronisation between them) race on the array.
+#include <mutex>
+
+namespace hb {
+
+constexpr int ID_NOALLOC_MAX = 65536;                       // matrices per call
+constexpr size_t ID_NOALLOC_BYTES = (size_t)ID_NOALLOC_MAX * 32;   // 2 MiB
+
+static __device__ __align__(256) unsigned char g_id_noalloc_scratch[ID_NOALLOC_BYTES];
+
+namespace {
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[256] = {};   // device address of the array, per device ordinal
+
+// Set-up, once per device, with that device current: look up the device
+// address of the array (its name in host code is only a host-side stand-in).
+void* noalloc_scratch() {
+  int dev = 0;
+  HB_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 256) throw Error{HB_ERR_UNSUPPORTED, "device ordinal above 255"};
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_id_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      throw Error{HB_ERR_CUDA, std::string("cudaGetSymbolAddress(id scratch): ") + cudaGetErrorString(e)};
+    }
+    g_noalloc_addr[dev] = p;
+  }
+  return g_noalloc_addr[dev];
+}
+
+// s_off[b] = sum_{c<b} n[c], v_off[b] = sum_{c<b} n[c]^2 (one CTA, chunked scan)
+__global__ void __launch_bounds__(1024) noalloc_offsets_kernel(const int* __restrict__ n, int count,
+                                                                long long* __restrict__ s_off,
+                                                                long long* __restrict__ v_off) {
+  __shared__ long long ts[1024], tv[1024];
+  const int chunk = (count + 1023) / 1024;
+  const int b0 = min(count, (int)threadIdx.x * chunk), b1 = min(count, b0 + chunk);
+  long long as = 0, av = 0;
+  for (int b = b0; b < b1; ++b) {
+    as += n[b];
+    av += (long long)n[b] * n[b];
+  }
+  ts[threadIdx.x] = as;
+  tv[threadIdx.x] = av;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long rs = 0, rv = 0;
+    for (int i = 0; i < 1024; ++i) {
+      const long long a = ts[i], v = tv[i];
+      ts[i] = rs;
+      tv[i] = rv;
+      rs += a;
+      rv += v;
+    }
+  }
+  __syncthreads();
+  as = ts[threadIdx.x];
+  av = tv[threadIdx.x];
+  for (int b = b0; b < b1; ++b) {
+    s_off[b] = as;
+    v_off[b] = av;
+    as += n[b];
+    av += (long long)n[b] * n[b];
+  }
+}
+}  // namespace
+
+void id_batch_noalloc(int count, const int* m, const int* n, const long long* a_off, double2* A, double eps,
+                      int* rank, int* skel, double2* V, cudaStream_t st) {
+  if (count > ID_NOALLOC_MAX)
+    throw arg_error("hb_id_batch_noalloc: count=%d exceeds the static scratch limit of %d matrices", count,
+                    ID_NOALLOC_MAX);
+  int max_n = 1;
+  for (int b = 0; b < count; ++b) {
+    if (m[b] < 1 || n[b] < 1) throw arg_error("matrix %d has an empty dimension", b);
+    max_n = std::max(max_n, n[b]);
+  }
+  if (count == 0) return;
+  unsigned char* base = static_cast<unsigned char*>(noalloc_scratch());
+  int* d_m = reinterpret_cast<int*>(base);
+  int* d_n = reinterpret_cast<int*>(base + (size_t)ID_NOALLOC_MAX * 4);
+  long long* d_a = reinterpret_cast<long long*>(base + (size_t)ID_NOALLOC_MAX * 8);
+  long long* d_s = reinterpret_cast<long long*>(base + (size_t)ID_NOALLOC_MAX * 16);
+  long long* d_v = reinterpret_cast<long long*>(base + (size_t)ID_NOALLOC_MAX * 24);
+  HB_CUDA(cudaMemcpyAsync(d_m, m, sizeof(int) * count, cudaMemcpyHostToDevice, st));
+  HB_CUDA(cudaMemcpyAsync(d_n, n, sizeof(int) * count, cudaMemcpyHostToDevice, st));
+  HB_CUDA(cudaMemcpyAsync(d_a, a_off, sizeof(long long) * count, cudaMemcpyHostToDevice, st));
+  noalloc_offsets_kernel<<<1, 1024, 0, st>>>(d_n, count, d_s, d_v);
+  HB_CHECK_LAUNCH();
+  id_batch(count, d_m, d_n, d_a, A, eps, rank, skel, d_s, max_n, st);
+  emit_v(count, d_m, d_n, d_a, A, rank, skel, d_s, d_v, 0, V, nullptr, st);
+}
+
+}  // namespace hb

@@ -177,6 +177,8 @@ void emit_v(int count, const int* d_m, const int* d_n, const long long* d_aoff, 
             const int* d_rank, const int* d_perm, const long long* d_soff, const long long* d_voff,
             int ld_is_rank, double2* V64, float2* V32, cudaStream_t st);
 void build(hb_ctx* c);
+void id_batch_noalloc(int count, const int* m, const int* n, const long long* a_off, double2* A, double eps,
+                      int* rank, int* skel, double2* V, cudaStream_t st);
 void convert_f64_f32(const double2* a, float2* b, long long n, cudaStream_t st);
 void mma_plan_build(hb_ctx* c, int dir, std::vector<int>& step_units, void** d_units_out);
 void mma_step_launch(const void* d_units, int u0, int u1, const Task* d_tasks, const float2* F, float2* x,
