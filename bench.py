@@ -135,7 +135,7 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    w = W.WORKLOADS[WORKLOAD]
+    w = W.WORKLOADS[args.workload]
     tab = load_tables(w)
     rows_per_step = 4
     times = []
@@ -169,7 +169,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     from paper_2210_02698_gb300 import binding, build
     build.build()
-    w = W.WORKLOADS[WORKLOAD]
+    w = W.WORKLOADS[args.workload]
     tab = load_tables(w)
     op = binding.Operator(w.N, tab["nodes"], tab["tau2"], tab["v0"], tab["v1"], w.n_cells(), w.omega,
                           eps=w.eps, leaf=w.leaf, chi=w.chi, precision=binding.HB_MIXED_BF16X3)
@@ -249,7 +249,7 @@ def run_ours(args):
     result = {}
     if rank == 0:
         hbm, peak_kind = peaks()
-        step_ms = sum(v[0] for k, v in ktimes.items() if k.startswith("bf_step")) / nk
+        step_ms = sum(v[0] for k, v in ktimes.items() if k.startswith("bf_")) / nk
         gather_ms = sum(v[0] for k, v in ktimes.items() if k in ("gather", "scatter")) / nk
         E = info["factor_entries"]
         fac_bytes = E * 8
@@ -265,6 +265,8 @@ def run_ours(args):
         cpu = {}
         rows_n = 8
         try:
+            if args.skip_cpu:
+                raise RuntimeError("skipped (--skip-cpu)")
             rows, U_ref, dt = cpu_oracle_sample(w, tab, rows_n)
             got = u_mixed.cpu().numpy().T[rows]
             got64 = u64.cpu().numpy().T[rows]
@@ -314,6 +316,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(W.WORKLOADS))
+    ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU oracle leg (profiling runs)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -40,8 +40,9 @@ void free_all(hb_ctx* c) {
   hb::dev_free(c->d_xh);
   hb::dev_free(c->d_tasks[0]);
   hb::dev_free(c->d_tasks[1]);
-  hb::dev_free(c->d_units[0]);
-  hb::dev_free(c->d_units[1]);
+  hb::flow_plan_free(c->flow_plan[0]);
+  hb::flow_plan_free(c->flow_plan[1]);
+  if (c->h_err) cudaFreeHost(c->h_err);
 }
 
 void check_vec_args(hb_ctx* c, const void* a, const void* b, int nrhs) {

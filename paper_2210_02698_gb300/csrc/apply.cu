@@ -162,11 +162,17 @@ void ensure_scratch(hb_ctx* c, int nrhs) {
   dev_free(c->d_xh);
   c->d_x = c->d_y = c->d_xh = nullptr;
   c->cap_rhs = 0;
-  c->d_x = dev_alloc<double2>((size_t)c->Nv * nrhs);
-  c->d_y = dev_alloc<double2>((size_t)c->Nv * nrhs);
-  c->d_xh = dev_alloc<double2>((size_t)std::max<long long>(c->xh_rows, 1) * nrhs);
+  // one spare row: 1D bulk copies round their size up to 16 bytes
+  c->d_x = dev_alloc<double2>((size_t)(c->Nv + 1) * nrhs);
+  c->d_y = dev_alloc<double2>((size_t)(c->Nv + 1) * nrhs);
+  c->d_xh = dev_alloc<double2>((size_t)(std::max<long long>(c->xh_rows, 1) + 1) * nrhs);
   c->cap_rhs = nrhs;
   if (!c->d_perm) c->d_perm = upload(c->perm);
+  if (!c->h_err) {
+    HB_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&c->h_err), sizeof(int), cudaHostAllocMapped));
+    *c->h_err = 0;
+    HB_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void**>(&c->d_err), c->h_err, 0));
+  }
   HB_CUDA(cudaDeviceSynchronize());
 }
 
@@ -186,38 +192,44 @@ void run_steps(hb_ctx* c, const C* F, int nrhs, int dir, cudaStream_t st, TimerS
 }  // namespace
 
 void apply_bf(hb_ctx* c, const double2* s, double2* u, int nrhs, int adjoint, int precision, cudaStream_t st) {
-  ensure_scratch(c, nrhs);
+  if (c->h_err && *reinterpret_cast<volatile int*>(c->h_err)) {
+    *reinterpret_cast<volatile int*>(c->h_err) = 0;
+    throw Error{HB_ERR_TIMEOUT, "a bounded device wait of an earlier apply gave up"};
+  }
+  const int chunk = (precision == HB_FP64) ? nrhs : std::min(nrhs, 64);
+  ensure_scratch(c, chunk);
   TimerScope ts{c, st, {}};
-  const long long total = c->Nv * nrhs;
-  const int grid = (int)std::min<long long>((total + 255) / 256, 152LL * 16);
   const double scale = c->h * c->h;
-  if (precision == HB_FP64) {
-    ts.begin("gather");
-    gather_kernel<double2><<<grid, 256, 0, st>>>(s, c->d_perm, (double2*)c->d_x, c->Nv, nrhs, scale);
-    HB_CHECK_LAUNCH();
-    ts.end();
-    run_steps<double2>(c, c->d_f64, nrhs, adjoint, st, ts);
-    ts.begin("scatter");
-    scatter_kernel<double2><<<grid, 256, 0, st>>>((double2*)c->d_y, c->d_perm, u, c->Nv, nrhs);
-    HB_CHECK_LAUNCH();
-    ts.end();
-  } else {
-    ts.begin("gather");
-    gather_kernel<float2><<<grid, 256, 0, st>>>(s, c->d_perm, (float2*)c->d_x, c->Nv, nrhs, scale);
-    HB_CHECK_LAUNCH();
-    ts.end();
-    const std::vector<int>& su = c->step_units[adjoint];
-    for (size_t k = 0; k + 1 < su.size(); ++k) {
-      if (su[k + 1] == su[k]) continue;
-      ts.begin(adjoint ? "bf_step_mma_adjoint" : "bf_step_mma");
-      mma_step_launch(c->d_units[adjoint], su[k], su[k + 1], c->d_tasks[adjoint], c->d_f32, (float2*)c->d_x,
-                      (float2*)c->d_y, (float2*)c->d_xh, nrhs, st);
+  for (int r0 = 0; r0 < nrhs; r0 += chunk) {
+    const int R = std::min(chunk, nrhs - r0);
+    const double2* sc = s + (size_t)r0 * c->Nv;
+    double2* uc = u + (size_t)r0 * c->Nv;
+    const long long total = c->Nv * R;
+    const int grid = (int)std::min<long long>((total + 255) / 256, 152LL * 16);
+    if (precision == HB_FP64) {
+      ts.begin("gather");
+      gather_kernel<double2><<<grid, 256, 0, st>>>(sc, c->d_perm, (double2*)c->d_x, c->Nv, R, scale);
+      HB_CHECK_LAUNCH();
+      ts.end();
+      run_steps<double2>(c, c->d_f64, R, adjoint, st, ts);
+      ts.begin("scatter");
+      scatter_kernel<double2><<<grid, 256, 0, st>>>((double2*)c->d_y, c->d_perm, uc, c->Nv, R);
+      HB_CHECK_LAUNCH();
+      ts.end();
+    } else {
+      ts.begin("gather");
+      gather_kernel<float2><<<grid, 256, 0, st>>>(sc, c->d_perm, (float2*)c->d_x, c->Nv, R, scale);
+      HB_CHECK_LAUNCH();
+      ts.end();
+      ts.begin(adjoint ? "bf_flow_adjoint" : "bf_flow");
+      flow_launch(c->flow_plan[adjoint], c->d_f32, (float2*)c->d_x, (float2*)c->d_y, (float2*)c->d_xh, R, c->d_err,
+                  c->opt.barrier_cycles > 0 ? c->opt.barrier_cycles : (1LL << 31), st);
+      ts.end();
+      ts.begin("scatter");
+      scatter_kernel<float2><<<grid, 256, 0, st>>>((float2*)c->d_y, c->d_perm, uc, c->Nv, R);
+      HB_CHECK_LAUNCH();
       ts.end();
     }
-    ts.begin("scatter");
-    scatter_kernel<float2><<<grid, 256, 0, st>>>((float2*)c->d_y, c->d_perm, u, c->Nv, nrhs);
-    HB_CHECK_LAUNCH();
-    ts.end();
   }
   ts.finish();
 }

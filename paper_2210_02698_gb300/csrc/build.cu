@@ -210,7 +210,7 @@ void build(hb_ctx* c) {
           br.skel.resize(r);
           for (int a = 0; a < r; ++a) br.skel[a] = jb.cols[hperm[hsoff[t] + a]];
           hvoff[t] = vacc;
-          vacc += (long long)r * hn[t];
+          vacc += ((long long)r * hn[t] + 1) & ~1LL;   // blocks start at even offsets (16-byte TMA alignment)
           max_rank = std::max(max_rank, r);
         }
         double2* seg = dev_alloc<double2>((size_t)vacc);
@@ -273,7 +273,7 @@ void build(hb_ctx* c) {
         EJob& e = ejobs[q];
         add_block(B, c, e.rows.data(), (long long)e.rows.size(), e.cols.data(), (long long)e.cols.size(), off);
         *e.target = nfac + off;
-        off += (long long)e.rows.size() * (long long)e.cols.size();
+        off += ((long long)e.rows.size() * (long long)e.cols.size() + 1) & ~1LL;
       }
       double2* seg = dev_alloc<double2>((size_t)off);
       run_blocks(c, B, seg, st);
@@ -287,14 +287,17 @@ void build(hb_ctx* c) {
 
   // pack the arenas
   c->n_factor = nfac;
-  c->d_f64 = dev_alloc<double2>((size_t)nfac);
+  // 16 spare elements: 1D bulk copies round their size up to 16 bytes
+  c->d_f64 = dev_alloc<double2>((size_t)nfac + 16);
+  HB_CUDA(cudaMemset(c->d_f64, 0, sizeof(double2) * ((size_t)nfac + 16)));
   for (const Segment& s : segs) {
     if (s.count) HB_CUDA(cudaMemcpyAsync(c->d_f64 + s.global_off, s.ptr, sizeof(double2) * s.count,
                                          cudaMemcpyDeviceToDevice, st));
   }
   HB_CUDA(cudaStreamSynchronize(st));
   for (const Segment& s : segs) dev_free(s.ptr);
-  c->d_f32 = dev_alloc<float2>((size_t)nfac);
+  c->d_f32 = dev_alloc<float2>((size_t)nfac + 16);
+  HB_CUDA(cudaMemset(c->d_f32, 0, sizeof(float2) * ((size_t)nfac + 16)));
   convert_f64_f32(c->d_f64, c->d_f32, nfac, st);
   HB_CUDA(cudaStreamSynchronize(st));
 
@@ -440,7 +443,187 @@ void build(hb_ctx* c) {
     begins.push_back((int)c->tasks_h[dir].size());
     c->step_begin[dir] = begins;
     c->d_tasks[dir] = upload(c->tasks_h[dir]);
-    mma_plan_build(c, dir, c->step_units[dir], &c->d_units[dir]);
+  }
+
+  // dataflow plans of the mixed apply (one persistent launch per apply)
+  {
+    // logical-task id of the producer of every block, per direction
+    std::vector<std::vector<std::vector<int>>> prod((size_t)bfs.size());
+    auto leaf_term = [&](long long t, int conj) {
+      FlowTerm ft{};
+      const long long p0 = node_lo(c, Lv, t);
+      const int sz = (int)(node_hi(c, Lv, t) - p0);
+      ft.f_off = leaf_off[(size_t)t];
+      ft.x_off = p0;
+      ft.r_in = sz;
+      ft.f_rows = sz;
+      ft.producer[0] = ft.producer[1] = -1;
+      ft.x_buf = 0;
+      ft.conj_t = (unsigned char)conj;
+      return ft;
+    };
+    // butterfly index of (HODBF level l, node oi as the row set)
+    auto bf_of_o = [&](int l, long long oi) { return (int)(((1LL << (l - 1)) - 1) * 2 + (oi >> 1) * 2 + (oi & 1)); };
+    auto bf_of_s = [&](int l, long long si) {
+      const long long p = si >> 1;
+      const int d = 1 - (int)(si & 1);   // o = 2p + d, s = 2p + 1 - d
+      return (int)(((1LL << (l - 1)) - 1) * 2 + p * 2 + d);
+    };
+    for (int dir = 0; dir < 2; ++dir) {
+      std::vector<FlowTask> ft;
+      for (size_t b = 0; b < bfs.size(); ++b) {
+        prod[b].assign(bfs[b].L + 1, {});
+        for (int k = 0; k <= bfs[b].L; ++k) prod[b][k].assign(bfs[b].lev[k].size(), -1);
+      }
+      if (dir == 0) {
+        for (int k = 0; k <= Lmax; ++k)
+          for (size_t bi = 0; bi < bfs.size(); ++bi) {
+            Butterfly& b = bfs[bi];
+            if (b.L < k) continue;
+            const int w = 1 << (b.L - k);
+            for (int i = 0; i < (1 << k); ++i)
+              for (int j = 0; j < w; ++j) {
+                BlockRec& br = b.lev[k][(size_t)i * w + j];
+                FlowTask t;
+                t.y_off = br.xh_off;
+                t.r_out = br.rank;
+                t.y_buf = 2;
+                FlowTerm tm{};
+                tm.f_off = br.f_off;
+                tm.f_rows = br.rank;
+                tm.conj_t = 0;
+                if (k == 0) {
+                  const long long n0 = node_lo(c, b.l + b.L, ((long long)b.si << b.L) + j);
+                  tm.x_off = n0;
+                  tm.r_in = (int)(node_hi(c, b.l + b.L, ((long long)b.si << b.L) + j) - n0);
+                  tm.x_buf = 0;
+                  tm.producer[0] = tm.producer[1] = -1;
+                } else {
+                  const size_t q1 = (size_t)(i / 2) * (2 * w) + 2 * j;
+                  const BlockRec& c1 = b.lev[k - 1][q1];
+                  const BlockRec& c2 = b.lev[k - 1][q1 + 1];
+                  tm.x_off = c1.xh_off;
+                  tm.r_in = c1.rank + c2.rank;
+                  tm.x_buf = 2;
+                  tm.producer[0] = prod[bi][k - 1][q1];
+                  tm.producer[1] = prod[bi][k - 1][q1 + 1];
+                }
+                t.terms.push_back(tm);
+                prod[bi][k][(size_t)i * w + j] = (int)ft.size();
+                ft.push_back(std::move(t));
+              }
+          }
+        for (long long t = 0; t < (1LL << Lv); ++t) {
+          FlowTask o;
+          o.y_off = node_lo(c, Lv, t);
+          o.r_out = (int)(node_hi(c, Lv, t) - o.y_off);
+          o.y_buf = 1;
+          o.terms.push_back(leaf_term(t, 0));
+          for (int l = 1; l <= Lv; ++l) {
+            const long long oi = t >> (Lv - l);
+            const int bi = bf_of_o(l, oi);
+            const Butterfly& b = bfs[(size_t)bi];
+            const long long i = t - (oi << b.L);
+            const BlockRec& br = b.lev[b.L][(size_t)i];
+            FlowTerm tm{};
+            tm.f_off = b.kl_off[(size_t)i];
+            tm.f_rows = o.r_out;
+            tm.x_off = br.xh_off;
+            tm.r_in = br.rank;
+            tm.x_buf = 2;
+            tm.producer[0] = prod[(size_t)bi][b.L][(size_t)i];
+            tm.producer[1] = -1;
+            o.terms.push_back(tm);
+          }
+          ft.push_back(std::move(o));
+        }
+      } else {
+        // depth 0: K^L^H
+        for (size_t bi = 0; bi < bfs.size(); ++bi) {
+          Butterfly& b = bfs[bi];
+          for (int i = 0; i < (1 << b.L); ++i) {
+            BlockRec& br = b.lev[b.L][(size_t)i];
+            const long long t0 = node_lo(c, b.l + b.L, ((long long)b.oi << b.L) + i);
+            const int sz = (int)(node_hi(c, b.l + b.L, ((long long)b.oi << b.L) + i) - t0);
+            FlowTask t;
+            t.y_off = br.xh_off;
+            t.r_out = br.rank;
+            t.y_buf = 2;
+            FlowTerm tm{};
+            tm.f_off = b.kl_off[(size_t)i];
+            tm.f_rows = sz;
+            tm.x_off = t0;
+            tm.r_in = sz;
+            tm.x_buf = 0;
+            tm.conj_t = 1;
+            tm.producer[0] = tm.producer[1] = -1;
+            t.terms.push_back(tm);
+            prod[bi][b.L][(size_t)i] = (int)ft.size();
+            ft.push_back(std::move(t));
+          }
+        }
+        // depth d: W^{L-d+1}^H, producing the pair of level L-d blocks
+        for (int d = 1; d <= Lmax; ++d)
+          for (size_t bi = 0; bi < bfs.size(); ++bi) {
+            Butterfly& b = bfs[bi];
+            if (b.L < d) continue;
+            const int t = b.L - d + 1;
+            const int w = 1 << (b.L - t);
+            for (int p = 0; p < (1 << (t - 1)); ++p)
+              for (int j = 0; j < w; ++j) {
+                const size_t q1 = (size_t)p * (2 * w) + 2 * j;
+                BlockRec& o1 = b.lev[t - 1][q1];
+                BlockRec& o2 = b.lev[t - 1][q1 + 1];
+                FlowTask tk;
+                tk.y_off = o1.xh_off;
+                tk.r_out = o1.rank + o2.rank;
+                tk.y_buf = 2;
+                for (int cc = 0; cc < 2; ++cc) {
+                  const size_t qb = (size_t)(2 * p + cc) * w + j;
+                  const BlockRec& br = b.lev[t][qb];
+                  FlowTerm tm{};
+                  tm.f_off = br.f_off;
+                  tm.f_rows = br.rank;
+                  tm.x_off = br.xh_off;
+                  tm.r_in = br.rank;
+                  tm.x_buf = 2;
+                  tm.conj_t = 1;
+                  tm.producer[0] = prod[bi][t][qb];
+                  tm.producer[1] = -1;
+                  tk.terms.push_back(tm);
+                }
+                prod[bi][t - 1][q1] = prod[bi][t - 1][q1 + 1] = (int)ft.size();
+                ft.push_back(std::move(tk));
+              }
+          }
+        for (long long t = 0; t < (1LL << Lv); ++t) {
+          FlowTask o;
+          o.y_off = node_lo(c, Lv, t);
+          o.r_out = (int)(node_hi(c, Lv, t) - o.y_off);
+          o.y_buf = 1;
+          o.terms.push_back(leaf_term(t, 1));
+          for (int l = 1; l <= Lv; ++l) {
+            const long long si = t >> (Lv - l);
+            const int bi = bf_of_s(l, si);
+            const Butterfly& b = bfs[(size_t)bi];
+            const long long j = t - (si << b.L);
+            const BlockRec& br = b.lev[0][(size_t)j];
+            FlowTerm tm{};
+            tm.f_off = br.f_off;
+            tm.f_rows = br.rank;
+            tm.x_off = br.xh_off;
+            tm.r_in = br.rank;
+            tm.x_buf = 2;
+            tm.conj_t = 1;
+            tm.producer[0] = prod[(size_t)bi][0][(size_t)j];
+            tm.producer[1] = -1;
+            o.terms.push_back(tm);
+          }
+          ft.push_back(std::move(o));
+        }
+      }
+      flow_plan_build(ft, &c->flow_plan[dir]);
+    }
   }
   HB_CUDA(cudaDeviceSynchronize());
 

@@ -94,6 +94,25 @@ struct Task {
   unsigned char conj_t, kind, pad0, pad1;
 };
 
+// Dataflow plan of the mixed apply (one persistent launch): a logical task
+// writes y_off .. y_off + r_out of buffer y_buf as the sum of its terms
+// op(F) X; a term's input rows were written by up to two earlier logical
+// tasks (`producer`, -1 = none).  Tasks are listed in dependency order.
+struct FlowTerm {
+  long long f_off;   // factor block start (element offset)
+  long long x_off;   // first input row
+  int r_in;          // input rows
+  int f_rows;        // stored rows of the block (r_out when !conj_t, r_in when conj_t)
+  int producer[2];
+  unsigned char x_buf, conj_t;
+};
+struct FlowTask {
+  long long y_off;
+  int r_out;
+  unsigned char y_buf;
+  std::vector<FlowTerm> terms;
+};
+
 // Host-side batch of ragged entry blocks (entries.cu).
 struct BlockMeta {
   long long row_off, m, col_off, n, out_off, seg_off, nseg, pad;
@@ -144,8 +163,9 @@ struct hb_ctx {
   std::vector<int> step_begin[2];
   std::vector<hb::Task> tasks_h[2];
   hb::Task* d_tasks[2] = {nullptr, nullptr};
-  std::vector<int> step_units[2];          // warp-unit ranges of the tensor-core steps
-  void* d_units[2] = {nullptr, nullptr};
+  void* flow_plan[2] = {nullptr, nullptr};  // tensor-core dataflow plans (bf_mma.cu)
+  int* h_err = nullptr;                    // mapped pinned error word of bounded device waits
+  int* d_err = nullptr;
   long long xh_rows = 0;
   int max_rank = 0;
 
@@ -180,9 +200,11 @@ void build(hb_ctx* c);
 void id_batch_noalloc(int count, const int* m, const int* n, const long long* a_off, double2* A, double eps,
                       int* rank, int* skel, double2* V, cudaStream_t st);
 void convert_f64_f32(const double2* a, float2* b, long long n, cudaStream_t st);
-void mma_plan_build(hb_ctx* c, int dir, std::vector<int>& step_units, void** d_units_out);
-void mma_step_launch(const void* d_units, int u0, int u1, const Task* d_tasks, const float2* F, float2* x,
-                     float2* y, float2* xh, int R, cudaStream_t st);
+void flow_plan_build(const std::vector<FlowTask>& tasks, void** plan_out);
+void flow_plan_free(void* plan);
+int flow_plan_ctas(const void* plan);
+void flow_launch(void* plan, const float2* F, float2* x, float2* y, float2* xh, int R, int* err,
+                 long long budget_cycles, cudaStream_t st);
 void apply_bf(hb_ctx* c, const double2* s, double2* u, int nrhs, int adjoint, int precision,
               cudaStream_t st);
 void tree_build(hb_ctx* c);
