@@ -218,16 +218,16 @@ void apply_bf(hb_ctx* c, const double2* s, double2* u, int nrhs, int adjoint, in
       ts.end();
     } else {
       ts.begin("gather");
-      gather_kernel<float2><<<grid, 256, 0, st>>>(sc, c->d_perm, (float2*)c->d_x, c->Nv, R, scale);
-      HB_CHECK_LAUNCH();
+      gather_pairs(sc, c->d_perm, (uint2*)c->d_x, c->Nv, R, scale, st);
       ts.end();
-      ts.begin(adjoint ? "bf_flow_adjoint" : "bf_flow");
-      flow_launch(c->flow_plan[adjoint], c->d_f32, (float2*)c->d_x, (float2*)c->d_y, (float2*)c->d_xh, R, c->d_err,
-                  c->opt.barrier_cycles > 0 ? c->opt.barrier_cycles : (1LL << 31), st);
-      ts.end();
+      // one launch per dependency depth; the timer brackets each launch
+      flow_launch(c->flow_plan[adjoint], c->d_pairs, (uint2*)c->d_x, (uint2*)c->d_y, (uint2*)c->d_xh, R, c->d_err,
+                  c->opt.barrier_cycles > 0 ? c->opt.barrier_cycles : (1LL << 31), st, [&](int, bool begin) {
+                    if (begin) ts.begin(adjoint ? "bf_tc_adjoint" : "bf_tc");
+                    else ts.end();
+                  });
       ts.begin("scatter");
-      scatter_kernel<float2><<<grid, 256, 0, st>>>((float2*)c->d_y, c->d_perm, uc, c->Nv, R);
-      HB_CHECK_LAUNCH();
+      scatter_pairs((const uint2*)c->d_y, c->d_perm, uc, c->Nv, R, st);
       ts.end();
     }
   }

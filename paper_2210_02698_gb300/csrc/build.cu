@@ -296,9 +296,9 @@ void build(hb_ctx* c) {
   }
   HB_CUDA(cudaStreamSynchronize(st));
   for (const Segment& s : segs) dev_free(s.ptr);
-  c->d_f32 = dev_alloc<float2>((size_t)nfac + 16);
-  HB_CUDA(cudaMemset(c->d_f32, 0, sizeof(float2) * ((size_t)nfac + 16)));
-  convert_f64_f32(c->d_f64, c->d_f32, nfac, st);
+  c->d_pairs = dev_alloc<uint2>((size_t)nfac + 16);
+  HB_CUDA(cudaMemset(c->d_pairs, 0, sizeof(uint2) * ((size_t)nfac + 16)));
+  convert_f64_pairs(c->d_f64, c->d_pairs, nfac, st);
   HB_CUDA(cudaStreamSynchronize(st));
 
   // xh offsets
@@ -487,6 +487,7 @@ void build(hb_ctx* c) {
                 FlowTask t;
                 t.y_off = br.xh_off;
                 t.r_out = br.rank;
+                t.depth = k;
                 t.y_buf = 2;
                 FlowTerm tm{};
                 tm.f_off = br.f_off;
@@ -517,6 +518,7 @@ void build(hb_ctx* c) {
           FlowTask o;
           o.y_off = node_lo(c, Lv, t);
           o.r_out = (int)(node_hi(c, Lv, t) - o.y_off);
+          o.depth = Lmax + 1;
           o.y_buf = 1;
           o.terms.push_back(leaf_term(t, 0));
           for (int l = 1; l <= Lv; ++l) {
@@ -548,6 +550,7 @@ void build(hb_ctx* c) {
             FlowTask t;
             t.y_off = br.xh_off;
             t.r_out = br.rank;
+            t.depth = 0;
             t.y_buf = 2;
             FlowTerm tm{};
             tm.f_off = b.kl_off[(size_t)i];
@@ -577,6 +580,7 @@ void build(hb_ctx* c) {
                 FlowTask tk;
                 tk.y_off = o1.xh_off;
                 tk.r_out = o1.rank + o2.rank;
+                tk.depth = d;
                 tk.y_buf = 2;
                 for (int cc = 0; cc < 2; ++cc) {
                   const size_t qb = (size_t)(2 * p + cc) * w + j;
@@ -600,6 +604,7 @@ void build(hb_ctx* c) {
           FlowTask o;
           o.y_off = node_lo(c, Lv, t);
           o.r_out = (int)(node_hi(c, Lv, t) - o.y_off);
+          o.depth = Lmax + 1;
           o.y_buf = 1;
           o.terms.push_back(leaf_term(t, 1));
           for (int l = 1; l <= Lv; ++l) {

@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdint>
 #include <cstdio>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -109,6 +110,7 @@ struct FlowTerm {
 struct FlowTask {
   long long y_off;
   int r_out;
+  int depth;          // dependency depth: inputs come from tasks of smaller depth only
   unsigned char y_buf;
   std::vector<FlowTerm> terms;
 };
@@ -155,10 +157,10 @@ struct hb_ctx {
   // build results
   bool built = false;
   hb_stats stats{};
-  // factor arenas: FP64 (double2) and mixed (float2), same element offsets
+  // factor arenas: FP64 (double2) and split-BF16 pairs (uint2), same element offsets
   long long n_factor = 0;
   double2* d_f64 = nullptr;
-  float2* d_f32 = nullptr;
+  uint2* d_pairs = nullptr;
   // apply plans: steps[0] forward, steps[1] adjoint; each step = task range
   std::vector<int> step_begin[2];
   std::vector<hb::Task> tasks_h[2];
@@ -199,12 +201,15 @@ void emit_v(int count, const int* d_m, const int* d_n, const long long* d_aoff, 
 void build(hb_ctx* c);
 void id_batch_noalloc(int count, const int* m, const int* n, const long long* a_off, double2* A, double eps,
                       int* rank, int* skel, double2* V, cudaStream_t st);
-void convert_f64_f32(const double2* a, float2* b, long long n, cudaStream_t st);
 void flow_plan_build(const std::vector<FlowTask>& tasks, void** plan_out);
 void flow_plan_free(void* plan);
-int flow_plan_ctas(const void* plan);
-void flow_launch(void* plan, const float2* F, float2* x, float2* y, float2* xh, int R, int* err,
-                 long long budget_cycles, cudaStream_t st);
+int flow_plan_depths(const void* plan);
+void flow_launch(void* plan, const uint2* F, uint2* x, uint2* y, uint2* xh, int R, int* err,
+                 long long budget_cycles, cudaStream_t st, const std::function<void(int, bool)>& timer);
+void convert_f64_pairs(const double2* a, uint2* b, long long n, cudaStream_t st);
+void gather_pairs(const double2* s, const long long* perm, uint2* x, long long Nv, int R, double scale,
+                  cudaStream_t st);
+void scatter_pairs(const uint2* y, const long long* perm, double2* u, long long Nv, int R, cudaStream_t st);
 void apply_bf(hb_ctx* c, const double2* s, double2* u, int nrhs, int adjoint, int precision,
               cudaStream_t st);
 void tree_build(hb_ctx* c);
