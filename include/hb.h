@@ -99,7 +99,8 @@ typedef struct {
   int max_rank;               /* largest butterfly rank r_{tau,nu}          */
   long long factor_entries;   /* complex entries of all factors + leaves    */
   long long factor_bytes_fp64;
-  long long factor_bytes_mixed;
+  long long factor_bytes_mixed; /* one direction's split-BF16 arena (8-row
+                                   tiles, rows padded to multiples of 8)   */
   long long id_blocks;        /* interpolative decompositions computed      */
   long long sampled_entries;  /* matrix entries evaluated by the build      */
   double build_ms;

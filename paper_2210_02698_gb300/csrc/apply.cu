@@ -6,8 +6,9 @@
 //   u  = y scattered back to natural order
 //
 // FP64 path: complex128 factors and vectors, one CTA per task, plain FP64
-// FMAs (the baseline).  Mixed path (HB_MIXED_BF16X3): FP32 factors and
-// vectors; see bf_mma.cu for the tensor-core step kernel.
+// FMAs (the baseline).  Mixed path (HB_MIXED_BF16X3): split-BF16 factors and
+// vectors in the MMA-fragment layout of bf_mma.cu, up to 32 right-hand
+// sides per pass.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -168,6 +169,12 @@ void ensure_scratch(hb_ctx* c, int nrhs) {
   c->d_xh = dev_alloc<double2>((size_t)(std::max<long long>(c->xh_rows, 1) + 1) * nrhs);
   c->cap_rhs = nrhs;
   if (!c->d_perm) c->d_perm = upload(c->perm);
+  if (!c->d_mx) {
+    // native vectors for two m-tiles: 2 KB per row tile
+    c->d_mx = dev_alloc<uint4>((size_t)std::max<long long>(c->nv_tiles, 1) * 128);
+    c->d_my = dev_alloc<uint4>((size_t)std::max<long long>(c->nv_tiles, 1) * 128);
+    c->d_mxh = dev_alloc<uint4>((size_t)std::max<long long>(c->xh_tiles, 1) * 128);
+  }
   if (!c->h_err) {
     HB_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&c->h_err), sizeof(int), cudaHostAllocMapped));
     *c->h_err = 0;
@@ -196,7 +203,7 @@ void apply_bf(hb_ctx* c, const double2* s, double2* u, int nrhs, int adjoint, in
     *reinterpret_cast<volatile int*>(c->h_err) = 0;
     throw Error{HB_ERR_TIMEOUT, "a bounded device wait of an earlier apply gave up"};
   }
-  const int chunk = (precision == HB_FP64) ? nrhs : std::min(nrhs, 64);
+  const int chunk = (precision == HB_FP64) ? nrhs : std::min(nrhs, 32);
   ensure_scratch(c, chunk);
   TimerScope ts{c, st, {}};
   const double scale = c->h * c->h;
@@ -217,17 +224,18 @@ void apply_bf(hb_ctx* c, const double2* s, double2* u, int nrhs, int adjoint, in
       HB_CHECK_LAUNCH();
       ts.end();
     } else {
+      const int MT = (R + 15) / 16;
       ts.begin("gather");
-      gather_pairs(sc, c->d_perm, (uint2*)c->d_x, c->Nv, R, scale, st);
+      gather_native(sc, c->d_pperm, c->d_mx, c->nv_tiles, c->Nv, R, MT, scale, st);
       ts.end();
       // one launch per dependency depth; the timer brackets each launch
-      flow_launch(c->flow_plan[adjoint], c->d_pairs, (uint2*)c->d_x, (uint2*)c->d_y, (uint2*)c->d_xh, R, c->d_err,
+      flow_launch(c->flow_plan[adjoint], c->d_nat[adjoint], c->d_mx, c->d_my, c->d_mxh, MT, c->d_err,
                   c->opt.barrier_cycles > 0 ? c->opt.barrier_cycles : (1LL << 31), st, [&](int, bool begin) {
                     if (begin) ts.begin(adjoint ? "bf_tc_adjoint" : "bf_tc");
                     else ts.end();
                   });
       ts.begin("scatter");
-      scatter_pairs((const uint2*)c->d_y, c->d_perm, uc, c->Nv, R, st);
+      scatter_native(c->d_my, c->d_pperm, uc, c->nv_tiles, c->Nv, R, MT, st);
       ts.end();
     }
   }

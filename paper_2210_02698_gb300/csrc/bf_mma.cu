@@ -2,43 +2,56 @@
 // (Sec. 4.2.1, Eq. butterfly_mat: every factor level is a batch of small
 // dense complex products Y = op(F) X; Sec. 4.2 HODBF sum).
 //
-// Storage.  Factors and vectors are kept as split-BF16 pairs: every complex
-// value a is 8 bytes {hi, lo}, hi = bf16x2(Re a, Im a), lo = bf16x2 of the
-// remainders a - hi, so that hi + lo keeps ~16 significant bits.  The pairs
-// feed the MMA fragments directly; products are
+// Numbers.  Every complex value a is a split-BF16 pair {hi, lo} (8 bytes):
+// hi = bf16x2(Re a, Im a), lo = bf16x2 of the remainders a - hi, so hi + lo
+// keeps ~16 significant bits.  Products are
 //     a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi          (split BF16 x 3)
-// with FP32 accumulation (mma.sync m16n8k16), and results are split again
-// when stored.
+// with FP32 accumulation (mma.sync m16n8k16), split again when stored.
 //
-// Complex -> real layout (k' = 2k + c interleaves real/imaginary parts):
+// Complex -> real.  With k' = 2k + c interleaving real/imaginary parts,
 //     D_r[m][n] = sum_k' A_r[m][k'] B[k'][n],   D_i[m][n] = sum_k' A_i[m][k'] B[k'][n]
 //     A_r[m][(2k,2k+1)] = (Re X[k][m], -Im X[k][m]),  A_i[m][(2k,2k+1)] = (Im X[k][m], Re X[k][m])
-//     B[(2k,2k+1)][n]   = (Re F[n][k], Im F[n][k])   (conj(F[k][n]) for op = ^H)
-// so a B register is a stored pair (im sign flipped for ^H), an A_r register
-// the X pair with the im sign flipped, an A_i register the X pair with its
-// halves swapped.  M = right-hand sides (16 per m-tile), N = 8 outputs per
-// n-tile, K = 8 complex inputs per k16 step.  Ranks pad to multiples of 8 in
-// registers only, never in memory.
+//     B[(2k,2k+1)][n]   = (Re F[n][k], Im F[n][k])
+// so a B register is a stored pair, an A_r register the X pair with the
+// imaginary sign flipped, an A_i register the X pair with its halves
+// swapped.  M = 16 right-hand sides (an m-tile), N = 8 outputs (an n-tile),
+// K = 8 complex inputs (a k-step).
+//
+// Native layout.  Factors and vectors live in HBM in the order the MMA
+// fragments want them, so that every fragment is one conflict-free 16-byte
+// shared-memory load per lane and no index is ever checked:
+//   * the k-slots t and t + 4 of lane (g, t) carry input rows 2t and 2t + 1
+//     of the k-step (any fixed order of k works; this one makes the
+//     accumulator of one step the A fragment of the next);
+//   * factor tile (k-step, n-tile) = 32 lanes x uint4
+//       {hi(F[n][2t]), hi(F[n][2t+1]), lo(F[n][2t]), lo(F[n][2t+1])},  n = g;
+//     tiles of a block ordered [k-step][n-tile]; the adjoint has its own
+//     arena holding F^H, so both directions run the same code;
+//   * vector tile (8 rows x 16 right-hand sides) = 32 lanes x uint4 of hi
+//     words, then 32 x uint4 of lo words, word j of lane (g, t) holding
+//     (row 2t + (j >> 1), right-hand side g + 8 (j & 1)); a buffer is
+//     [row tile][m-tile] of such tiles.
+// Rows of every block part (a leaf, a skeleton) are padded to a multiple of
+// 8 with zeros; padded rows of the vectors stay exactly zero.
 //
 // Work units.  A "piece" is what one shared-memory stage holds: up to
-// PB_MAX factor chunks (each a contiguous run of a column-major block) and
-// up to PX_MAX runs of input rows, all fetched with cp.async.bulk (1D TMA)
-// on one mbarrier.  Mode 0: the chunks are independent products with their
-// own outputs (e.g. the V^0 blocks of all butterflies that read the same
-// leaf, or runs of neighbouring transfer blocks); mode 1: all chunks
-// accumulate into one output (a leaf's dense block plus its K^L terms, or
-// one large block cut into column chunks), possibly over several pieces.
+// PB_MAX factor chunks (a run of k-steps of one block, contiguous in the
+// arena) and up to PX_MAX runs of input row tiles, fetched with
+// cp.async.bulk (1D TMA) on one mbarrier.  Mode 0: the chunks are
+// independent products with their own outputs (e.g. the V^0 blocks that
+// read the same leaf); mode 1: all chunks accumulate into one output (a
+// leaf's dense block plus its K^L terms, or one large block cut into
+// k-chunks), possibly over several pieces.
 //
 // Scheduling.  Pieces are grouped by dependency depth (depth d only reads
 // outputs of depths < d); one persistent kernel per depth, CTA b running its
 // share of the depth's pieces (the pieces of one accumulating task stay on
-// one CTA, in order); a producer warp streams pieces through a
-// FLOW_STAGES-deep ring, NCW consumer warps compute.  Depth kernels are
-// chained with programmatic dependent launch: a kernel's CTAs start as the
-// previous depth drains, prefetch their first factor chunks (constant data)
-// and only then wait (griddepcontrol.wait) before copying inputs the
-// previous depth wrote.  Every wait is bounded by a per-thread deadline;
-// past it the mapped error word is set.
+// one CTA, in order); a producer warp streams pieces through a ring of
+// stages, NCW consumer warps compute.  Depth kernels are chained with
+// programmatic dependent launch: a kernel's CTAs prefetch their first factor
+// chunks (constant data) and only then wait (griddepcontrol.wait) before
+// copying inputs the previous depth wrote.  Every wait is bounded by a
+// per-thread deadline; past it the mapped error word is set.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -50,38 +63,35 @@
 
 namespace hb {
 
-constexpr int NCW = 8;                  // consumer warps
-constexpr int TMA_MAX_NT = 4;           // n-tiles per work item (outputs per item <= 32)
-constexpr int PB_MAX = 8;               // factor chunks per piece
-constexpr int PX_MAX = 8;               // input runs per piece
-constexpr int FLOW_STAGES = 3;
-constexpr int F_CAP = 32768;            // factor bytes per piece
-constexpr int X_CAP_ROWS = 160;         // input rows per piece
-constexpr int MAX_OUT = 8 * TMA_MAX_NT * NCW;   // outputs of one block / accumulating task
-constexpr uint32_t IM_SIGN = 0x80000000u;       // sign bit of the imaginary (upper) bf16
+constexpr int NCW = 8;                 // consumer warps
+constexpr int PB_MAX = 8;              // factor chunks per piece
+constexpr int PX_MAX = 8;              // input runs per piece
+constexpr int MAX_STAGES = 4;
+constexpr int F_CAP_TILES = 96;        // factor tiles (512 bytes) per piece
+constexpr int X_CAP_TILES = 24;        // input row tiles per piece
+constexpr int MAX_NT = 32;             // n-tiles of one output (256 rows)
+constexpr uint32_t IM_SIGN = 0x80000000u;   // sign bit of the imaginary (upper) bf16
 
 struct PBlk {            // one factor chunk of a piece (32 bytes)
-  long long f_off;       // element offset of the contiguous chunk
-  long long y_off;       // mode 0: first output row
-  int f_rows;            // stored rows (leading dimension)
-  int f_cols;            // stored columns
-  short xc;              // input run of this chunk
-  short x_row;           // first row inside that run
-  short r_out;           // mode 0: outputs
-  unsigned char conj_t;  // op = ^H
-  unsigned char y_buf;   // mode 0: output buffer
+  long long f_tile;      // first factor tile
+  long long y_tile;      // mode 0: first output row tile
+  int nt;                // n-tiles of the block
+  int ks;                // k-steps of the chunk
+  short xc;              // input run (-1: none)
+  short x_t;             // first row tile inside that run
+  int y_buf;             // mode 0: output buffer
 };
 
-struct PXc {             // one run of input rows (16 bytes)
-  long long x_off;
-  int rows;
+struct PXc {             // one run of input row tiles (16 bytes)
+  long long x_tile;
+  int tiles;
   int buf;
 };
 
 struct PRec {            // one piece, 512 bytes
   int nb, nx, mode, first_last;
-  long long y_off;       // mode 1 output
-  int r_out, y_buf;
+  long long y_tile;      // mode 1 output
+  int nt, y_buf;
   PBlk blk[PB_MAX];
   PXc xc[PX_MAX];
   unsigned char pad[512 - 32 - PB_MAX * 32 - PX_MAX * 16];
@@ -92,7 +102,7 @@ static_assert(sizeof(PRec) == 512, "PRec layout");
 struct StageMeta {
   PRec rec;
   int f_soff[PB_MAX];    // byte offset of each chunk in the stage
-  int x_soff[PX_MAX];    // byte offset of each run's first row in the stage
+  int x_soff[PX_MAX];    // byte offset of each run in the stage
 };
 
 // ------------------------------------------------------------ helpers ----
@@ -169,117 +179,127 @@ __device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t
 struct StepArgs {
   const PRec* recs;
   const long long* cta_off;   // pieces of CTA b: [cta_off[b], cta_off[b+1])
-  const uint2* F;
-  uint2* x;
-  uint2* y;
-  uint2* xh;
-  int R;
+  const uint4* F;
+  uint4* x;
+  uint4* y;
+  uint4* xh;
+  int stages;
   int stage_bytes;
   long long budget;
   int* err;
 };
 
-// One warp's share of one factor chunk: n-tiles [t0, t0 + ntl), accumulated
-// into acc (MT m-tiles of 16 right-hand sides).
+// n-tiles per warp item: 8 / MT keeps the accumulators at 64 registers
 template <int MT>
-__device__ __forceinline__ void chunk_mma(const uint2* Fs, const uint2* Xs, int f_rows, int kr, int r_out,
-                                          int conj, int t0, int ntl, int R, int g, int t,
-                                          float (&acc_r)[TMA_MAX_NT][MT][4], float (&acc_i)[TMA_MAX_NT][MT][4]) {
-  const uint32_t cs = conj ? IM_SIGN : 0u;
-  for (int kb = 0; kb < kr; kb += 8) {
-    const int k0 = kb + t, k1 = kb + t + 4;
-    uint32_t bh0[TMA_MAX_NT], bl0[TMA_MAX_NT], bh1[TMA_MAX_NT], bl1[TMA_MAX_NT];
+struct Tiles {
+  static constexpr int NTW = 8 / MT;
+};
+
+// Accumulate ks k-steps of a chunk into acc: n-tiles [t0, t0 + NTL) of a
+// block with nt n-tiles (Fs: its first k-step), input tiles Xs.  NTL is a
+// compile-time count so that no MMA slot is issued for an absent tile.
+template <int MT, int NTL>
+__device__ __forceinline__ void chunk_mma_n(const uint4* __restrict__ Fs, const uint4* __restrict__ Xs, int nt,
+                                            int ks, int t0, int lane, float (&acc)[Tiles<MT>::NTW][MT][8]) {
+  const uint4* fp = Fs + t0 * 32 + lane;
+  const uint4* xp = Xs + lane;
+  for (int k = 0; k < ks; ++k, fp += nt * 32, xp += MT * 64) {
+    uint4 b[NTL];
 #pragma unroll
-    for (int j = 0; j < TMA_MAX_NT; ++j) {
-      const int n = 8 * (t0 + j) + g;
-      uint2 v0 = make_uint2(0u, 0u), v1 = v0;
-      if (j < ntl && n < r_out) {
-        if (!conj) {
-          if (k0 < kr) v0 = Fs[k0 * f_rows + n];
-          if (k1 < kr) v1 = Fs[k1 * f_rows + n];
-        } else {
-          if (k0 < kr) v0 = Fs[n * f_rows + k0];
-          if (k1 < kr) v1 = Fs[n * f_rows + k1];
+    for (int j = 0; j < NTL; ++j) b[j] = fp[j * 32];
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt) {
+      const uint4 h = xp[mt * 64], l = xp[mt * 64 + 32];
+      const uint32_t arh[4] = {h.x ^ IM_SIGN, h.y ^ IM_SIGN, h.z ^ IM_SIGN, h.w ^ IM_SIGN};
+      const uint32_t arl[4] = {l.x ^ IM_SIGN, l.y ^ IM_SIGN, l.z ^ IM_SIGN, l.w ^ IM_SIGN};
+      const uint32_t aih[4] = {__byte_perm(h.x, 0, 0x1032), __byte_perm(h.y, 0, 0x1032),
+                               __byte_perm(h.z, 0, 0x1032), __byte_perm(h.w, 0, 0x1032)};
+      const uint32_t ail[4] = {__byte_perm(l.x, 0, 0x1032), __byte_perm(l.y, 0, 0x1032),
+                               __byte_perm(l.z, 0, 0x1032), __byte_perm(l.w, 0, 0x1032)};
+#pragma unroll
+      for (int j = 0; j < NTL; ++j) {
+        float* ar = acc[j][mt];
+        float* ai = acc[j][mt] + 4;
+        mma16816(ar, arh, b[j].x, b[j].y);
+        mma16816(ar, arh, b[j].z, b[j].w);
+        mma16816(ar, arl, b[j].x, b[j].y);
+        mma16816(ai, aih, b[j].x, b[j].y);
+        mma16816(ai, aih, b[j].z, b[j].w);
+        mma16816(ai, ail, b[j].x, b[j].y);
+      }
+    }
+  }
+}
+
+template <int MT>
+__device__ __forceinline__ void chunk_mma(const uint4* __restrict__ Fs, const uint4* __restrict__ Xs, int nt,
+                                          int ks, int t0, int ntl, int lane,
+                                          float (&acc)[Tiles<MT>::NTW][MT][8]) {
+  switch (ntl) {
+    case 1: chunk_mma_n<MT, 1>(Fs, Xs, nt, ks, t0, lane, acc); break;
+    case 2: chunk_mma_n<MT, 2>(Fs, Xs, nt, ks, t0, lane, acc); break;
+    case 3: chunk_mma_n<MT, 3>(Fs, Xs, nt, ks, t0, lane, acc); break;
+    case 4: chunk_mma_n<MT, 4>(Fs, Xs, nt, ks, t0, lane, acc); break;
+    default:
+      if constexpr (Tiles<MT>::NTW > 4) {
+        switch (ntl) {
+          case 5: chunk_mma_n<MT, 5>(Fs, Xs, nt, ks, t0, lane, acc); break;
+          case 6: chunk_mma_n<MT, 6>(Fs, Xs, nt, ks, t0, lane, acc); break;
+          case 7: chunk_mma_n<MT, 7>(Fs, Xs, nt, ks, t0, lane, acc); break;
+          case 8: chunk_mma_n<MT, 8>(Fs, Xs, nt, ks, t0, lane, acc); break;
+          default: break;
         }
       }
-      bh0[j] = v0.x ^ cs;
-      bl0[j] = v0.y ^ cs;
-      bh1[j] = v1.x ^ cs;
-      bl1[j] = v1.y ^ cs;
-    }
-#pragma unroll
-    for (int aa = 0; aa < MT; ++aa) {
-      const int mA = aa * 16 + g, mB = mA + 8;
-      uint2 x00 = make_uint2(0u, 0u), x01 = x00, x10 = x00, x11 = x00;
-      if (k0 < kr) {
-        if (mA < R) x00 = Xs[k0 * R + mA];
-        if (mB < R) x01 = Xs[k0 * R + mB];
-      }
-      if (k1 < kr) {
-        if (mA < R) x10 = Xs[k1 * R + mA];
-        if (mB < R) x11 = Xs[k1 * R + mB];
-      }
-      const uint32_t arh[4] = {x00.x ^ IM_SIGN, x01.x ^ IM_SIGN, x10.x ^ IM_SIGN, x11.x ^ IM_SIGN};
-      const uint32_t arl[4] = {x00.y ^ IM_SIGN, x01.y ^ IM_SIGN, x10.y ^ IM_SIGN, x11.y ^ IM_SIGN};
-      const uint32_t aih[4] = {__byte_perm(x00.x, 0, 0x1032), __byte_perm(x01.x, 0, 0x1032),
-                               __byte_perm(x10.x, 0, 0x1032), __byte_perm(x11.x, 0, 0x1032)};
-      const uint32_t ail[4] = {__byte_perm(x00.y, 0, 0x1032), __byte_perm(x01.y, 0, 0x1032),
-                               __byte_perm(x10.y, 0, 0x1032), __byte_perm(x11.y, 0, 0x1032)};
-#pragma unroll
-      for (int j = 0; j < TMA_MAX_NT; ++j) {
-        if (j >= ntl) break;
-        mma16816(acc_r[j][aa], arh, bh0[j], bh1[j]);
-        mma16816(acc_r[j][aa], arh, bl0[j], bl1[j]);
-        mma16816(acc_r[j][aa], arl, bh0[j], bh1[j]);
-        mma16816(acc_i[j][aa], aih, bh0[j], bh1[j]);
-        mma16816(acc_i[j][aa], aih, bl0[j], bl1[j]);
-        mma16816(acc_i[j][aa], ail, bh0[j], bh1[j]);
-      }
-    }
+      break;
   }
 }
 
+// Store n-tiles [t0, t0 + ntl) of the accumulators as vector tiles at Y.
+// Accumulator element e of lane (g, t) is (right-hand side g + 8 (e >> 1),
+// output 2t + (e & 1)); vector word j holds (row 2t + (j >> 1), right-hand
+// side g + 8 (j & 1)), so words (0, 1, 2, 3) = elements (0, 2, 1, 3).
 template <int MT>
-__device__ __forceinline__ void store_tiles(uint2* out, int t0, int ntl, int r_out, int R, int g, int t,
-                                            const float (&acc_r)[TMA_MAX_NT][MT][4],
-                                            const float (&acc_i)[TMA_MAX_NT][MT][4]) {
+__device__ __forceinline__ void store_tiles(uint4* Y, int t0, int ntl, int lane,
+                                            const float (&acc)[Tiles<MT>::NTW][MT][8]) {
+  constexpr int NTW = Tiles<MT>::NTW;
 #pragma unroll
-  for (int j = 0; j < TMA_MAX_NT; ++j) {
+  for (int j = 0; j < NTW; ++j) {
     if (j >= ntl) break;
 #pragma unroll
-    for (int aa = 0; aa < MT; ++aa) {
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int mm = aa * 16 + g + ((e & 2) ? 8 : 0);
-        const int n = 8 * (t0 + j) + 2 * t + (e & 1);
-        if (mm < R && n < r_out) out[(size_t)n * R + mm] = to_pair(acc_r[j][aa][e], acc_i[j][aa][e]);
-      }
+    for (int mt = 0; mt < MT; ++mt) {
+      const float* a = acc[j][mt];
+      const uint2 p0 = to_pair(a[0], a[4]), p1 = to_pair(a[1], a[5]);
+      const uint2 p2 = to_pair(a[2], a[6]), p3 = to_pair(a[3], a[7]);
+      uint4* o = Y + ((size_t)(t0 + j) * MT + mt) * 64;
+      o[lane] = make_uint4(p0.x, p2.x, p1.x, p3.x);
+      o[32 + lane] = make_uint4(p0.y, p2.y, p1.y, p3.y);
     }
   }
 }
 
 template <int MT>
-__device__ __forceinline__ void zero_acc(float (&acc_r)[TMA_MAX_NT][MT][4], float (&acc_i)[TMA_MAX_NT][MT][4]) {
+__device__ __forceinline__ void zero_acc(float (&acc)[Tiles<MT>::NTW][MT][8]) {
 #pragma unroll
-  for (int j = 0; j < TMA_MAX_NT; ++j)
+  for (int j = 0; j < Tiles<MT>::NTW; ++j)
 #pragma unroll
-    for (int aa = 0; aa < MT; ++aa)
+    for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
-      for (int e = 0; e < 4; ++e) acc_r[j][aa][e] = acc_i[j][aa][e] = 0.f;
+      for (int e = 0; e < 8; ++e) acc[j][mt][e] = 0.f;
 }
 
 // ------------------------------------------------------------- kernel ----
 template <int MT>
 __global__ void __launch_bounds__((NCW + 1) * 32, 1) bf_step_kernel(StepArgs a) {
+  constexpr int NTW = Tiles<MT>::NTW;
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ uint64_t full[FLOW_STAGES], empty[FLOW_STAGES];
-  __shared__ __align__(16) StageMeta meta[FLOW_STAGES];
+  __shared__ uint64_t full[MAX_STAGES], empty[MAX_STAGES];
+  __shared__ __align__(16) StageMeta meta[MAX_STAGES];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int R = a.R;
+  const int nst = a.stages;
   auto buf = [&](int id) { return id == 0 ? a.x : (id == 1 ? a.y : a.xh); };
 
   if (tid == 0) {
-    for (int s = 0; s < FLOW_STAGES; ++s) {
+    for (int s = 0; s < nst; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], NCW);
     }
@@ -298,45 +318,38 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) bf_step_kernel(StepArgs a) 
     const int4* src = reinterpret_cast<const int4*>(a.recs + rb);
     int4 nxt = (npc > 0) ? src[lane] : make_int4(0, 0, 0, 0);
     for (long long i = 0; i < npc; ++i) {
-      const int s = (int)(i % FLOW_STAGES);
+      const int s = (int)(i % nst);
       const int4 cur = nxt;
       if (i + 1 < npc) nxt = src[(i + 1) * 32 + lane];   // prefetch the next record
-      if (i >= FLOW_STAGES) mbar_wait_until(&empty[s], (uint32_t)(((i / FLOW_STAGES) - 1) & 1), deadline, a.err);
+      if (i >= nst) mbar_wait_until(&empty[s], (uint32_t)(((i / nst) - 1) & 1), deadline, a.err);
       reinterpret_cast<int4*>(&meta[s].rec)[lane] = cur;
       __syncwarp();
       if (lane == 0) {
         StageMeta& m = meta[s];
         const PRec& r = m.rec;
         unsigned char* st = smem + (size_t)s * a.stage_bytes;
-        uint32_t off = 0, total = 0;
-        uint32_t fb[PB_MAX];
+        uint32_t off = 0;
         for (int b = 0; b < r.nb; ++b) {
-          fb[b] = (uint32_t)((r.blk[b].f_rows * r.blk[b].f_cols * 8 + 15) & ~15);
           m.f_soff[b] = (int)off;
-          off += (fb[b] + 127) & ~127u;
-          total += fb[b];
+          off += (uint32_t)(r.blk[b].nt * r.blk[b].ks) * 512u;
         }
-        uint32_t xb[PX_MAX], xdst[PX_MAX];
-        const char* xsrc[PX_MAX];
         for (int c = 0; c < r.nx; ++c) {
-          const char* xs = reinterpret_cast<const char*>(buf(r.xc[c].buf) + (size_t)r.xc[c].x_off * R);
-          const uintptr_t al = reinterpret_cast<uintptr_t>(xs) & ~(uintptr_t)15;
-          const int pad = (int)(reinterpret_cast<uintptr_t>(xs) - al);
-          xb[c] = (uint32_t)((pad + r.xc[c].rows * R * 8 + 15) & ~15);
-          xsrc[c] = reinterpret_cast<const char*>(al);
-          xdst[c] = off;
-          m.x_soff[c] = (int)off + pad;
-          off += (xb[c] + 127) & ~127u;
-          total += xb[c];
+          m.x_soff[c] = (int)off;
+          off += (uint32_t)r.xc[c].tiles * (uint32_t)(MT * 1024);
         }
-        mbar_expect_tx(&full[s], total);
-        for (int b = 0; b < r.nb; ++b) tma_load_1d(st + m.f_soff[b], a.F + r.blk[b].f_off, fb[b], &full[s]);
+        mbar_expect_tx(&full[s], off);
+        for (int b = 0; b < r.nb; ++b) {
+          const uint32_t fb = (uint32_t)(r.blk[b].nt * r.blk[b].ks) * 512u;
+          if (fb) tma_load_1d(st + m.f_soff[b], a.F + r.blk[b].f_tile * 32, fb, &full[s]);
+        }
         if (!waited) {
           asm volatile("griddepcontrol.wait;" ::: "memory");
           asm volatile("fence.proxy.async.global;" ::: "memory");
           waited = true;
         }
-        for (int c = 0; c < r.nx; ++c) tma_load_1d(st + xdst[c], xsrc[c], xb[c], &full[s]);
+        for (int c = 0; c < r.nx; ++c)
+          tma_load_1d(st + m.x_soff[c], buf(r.xc[c].buf) + r.xc[c].x_tile * (MT * 64),
+                      (uint32_t)r.xc[c].tiles * (uint32_t)(MT * 1024), &full[s]);
       }
       __syncwarp();
     }
@@ -345,12 +358,10 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) bf_step_kernel(StepArgs a) 
   }
 
   // -------------------------------------------------------------- consumers
-  const int g = lane >> 2, t = lane & 3;
-  float acc_r[TMA_MAX_NT][MT][4];
-  float acc_i[TMA_MAX_NT][MT][4];
+  float acc[NTW][MT][8];
   for (long long i = 0; i < npc; ++i) {
-    const int s = (int)(i % FLOW_STAGES);
-    const bool ok = mbar_wait_until(&full[s], (uint32_t)((i / FLOW_STAGES) & 1), deadline, a.err);
+    const int s = (int)(i % nst);
+    const bool ok = mbar_wait_until(&full[s], (uint32_t)((i / nst) & 1), deadline, a.err);
     const StageMeta& m = meta[s];
     const PRec& r = m.rec;
     const unsigned char* st = smem + (size_t)s * a.stage_bytes;
@@ -358,38 +369,37 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) bf_step_kernel(StepArgs a) 
     if (r.mode == 0) {
       // independent chunks: work items (chunk, up to ipt n-tiles) dealt to the warps
       int total_tiles = 0;
-      for (int b = 0; b < nb; ++b) total_tiles += (r.blk[b].r_out + 7) >> 3;
-      const int ipt = max(1, min(TMA_MAX_NT, (total_tiles + NCW - 1) / NCW));
+      for (int b = 0; b < nb; ++b) total_tiles += r.blk[b].nt;
+      const int ipt = max(1, min(NTW, (total_tiles + NCW - 1) / NCW));
       int item = 0;
       for (int b = 0; b < nb; ++b) {
         const PBlk& B = r.blk[b];
-        const int nt = (B.r_out + 7) >> 3;
-        for (int t0 = 0; t0 < nt; t0 += ipt, ++item) {
+        for (int t0 = 0; t0 < B.nt; t0 += ipt, ++item) {
           if (item % NCW != warp) continue;
-          const int ntl = min(ipt, nt - t0);
-          zero_acc<MT>(acc_r, acc_i);
-          const uint2* Fs = reinterpret_cast<const uint2*>(st + m.f_soff[b]);
-          const uint2* Xs = reinterpret_cast<const uint2*>(st + m.x_soff[B.xc]) + (size_t)B.x_row * R;
-          const int kr = B.conj_t ? B.f_rows : B.f_cols;
-          chunk_mma<MT>(Fs, Xs, B.f_rows, kr, B.r_out, B.conj_t, t0, ntl, R, g, t, acc_r, acc_i);
-          store_tiles<MT>(buf(B.y_buf) + (size_t)B.y_off * R, t0, ntl, B.r_out, R, g, t, acc_r, acc_i);
+          const int ntl = min(ipt, B.nt - t0);
+          zero_acc<MT>(acc);
+          if (B.xc >= 0) {
+            const uint4* Fs = reinterpret_cast<const uint4*>(st + m.f_soff[b]);
+            const uint4* Xs = reinterpret_cast<const uint4*>(st + m.x_soff[B.xc]) + (size_t)B.x_t * MT * 64;
+            chunk_mma<MT>(Fs, Xs, B.nt, B.ks, t0, ntl, lane, acc);
+          }
+          store_tiles<MT>(buf(B.y_buf) + (size_t)B.y_tile * MT * 64, t0, ntl, lane, acc);
         }
       }
     } else {
       // every chunk accumulates into one output; warp w owns a contiguous tile range
-      const int r_out = r.r_out, nt = (r_out + 7) >> 3;
-      const int ipt = max(1, min(TMA_MAX_NT, (nt + NCW - 1) / NCW));
-      const int t0 = warp * ipt, ntl = max(0, min(ipt, nt - t0));
-      if (r.first_last & 1) zero_acc<MT>(acc_r, acc_i);
+      const int ipt = max(1, min(NTW, (r.nt + NCW - 1) / NCW));
+      const int t0 = warp * ipt, ntl = max(0, min(ipt, r.nt - t0));
+      if (r.first_last & 1) zero_acc<MT>(acc);
       if (ntl > 0) {
         for (int b = 0; b < nb; ++b) {
           const PBlk& B = r.blk[b];
-          const uint2* Fs = reinterpret_cast<const uint2*>(st + m.f_soff[b]);
-          const uint2* Xs = reinterpret_cast<const uint2*>(st + m.x_soff[B.xc]) + (size_t)B.x_row * R;
-          const int kr = B.conj_t ? B.f_rows : B.f_cols;
-          chunk_mma<MT>(Fs, Xs, B.f_rows, kr, r_out, B.conj_t, t0, ntl, R, g, t, acc_r, acc_i);
+          if (B.xc < 0) continue;
+          const uint4* Fs = reinterpret_cast<const uint4*>(st + m.f_soff[b]);
+          const uint4* Xs = reinterpret_cast<const uint4*>(st + m.x_soff[B.xc]) + (size_t)B.x_t * MT * 64;
+          chunk_mma<MT>(Fs, Xs, B.nt, B.ks, t0, ntl, lane, acc);
         }
-        if (r.first_last & 2) store_tiles<MT>(buf(r.y_buf) + (size_t)r.y_off * R, t0, ntl, r_out, R, g, t, acc_r, acc_i);
+        if (r.first_last & 2) store_tiles<MT>(buf(r.y_buf) + (size_t)r.y_tile * MT * 64, t0, ntl, lane, acc);
       }
     }
     __syncwarp();
@@ -398,55 +408,120 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) bf_step_kernel(StepArgs a) 
 }
 
 // --------------------------------------------------- conversions / I/O ----
-__global__ void f64_to_pair_kernel(const double2* __restrict__ a, uint2* __restrict__ b, long long n) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x)
-    b[i] = to_pair((float)a[i].x, (float)a[i].y);
+__device__ __forceinline__ int part_index(int pos, int r1, int r2) {
+  const int p1 = (r1 + 7) & ~7;
+  if (pos < p1) return pos < r1 ? pos : -1;
+  return (pos - p1 < r2) ? r1 + pos - p1 : -1;
 }
 
-// x[p][r] = pair(scale * s[r*Nv + perm[p]])
-__global__ void gather_pair_kernel(const double2* __restrict__ s, const long long* __restrict__ perm,
-                                   uint2* __restrict__ x, long long Nv, int R, double scale) {
-  const long long total = Nv * R;
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const long long p = idx / R;
-    const int r = (int)(idx % R);
-    const double2 v = s[(size_t)r * Nv + perm[p]];
-    x[idx] = to_pair((float)(v.x * scale), (float)(v.y * scale));
+// One CTA per native block: tile (k-step, n-tile), lane (g, t) ->
+// {hi F[n][2t], hi F[n][2t+1], lo F[n][2t], lo F[n][2t+1]} with n = 8 n-tile + g.
+__global__ void nat_convert_kernel(const double2* __restrict__ F, const NatBlock* __restrict__ blocks,
+                                   uint4* __restrict__ out) {
+  const NatBlock B = blocks[blockIdx.x];
+  const int nt = (B.r1 + 7) / 8 + (B.r2 + 7) / 8, ks = (B.k1 + 7) / 8 + (B.k2 + 7) / 8;
+  for (int idx = threadIdx.x; idx < nt * ks * 32; idx += blockDim.x) {
+    const int tile = idx >> 5, lane = idx & 31, g = lane >> 2, t = lane & 3;
+    const int kstep = tile / nt, ntile = tile % nt;
+    const int n = part_index(8 * ntile + g, B.r1, B.r2);
+    uint2 p[2];
+    for (int h = 0; h < 2; ++h) {
+      const int k = part_index(8 * kstep + 2 * t + h, B.k1, B.k2);
+      double re = 0, im = 0;
+      if (n >= 0 && k >= 0) {
+        if (B.conj) {
+          const double2 v = F[B.src_off + k + (long long)n * B.ld];
+          re = v.x;
+          im = -v.y;
+        } else {
+          const double2 v = F[B.src_off + n + (long long)k * B.ld];
+          re = v.x;
+          im = v.y;
+        }
+      }
+      p[h] = to_pair((float)re, (float)im);
+    }
+    out[(B.tile0 + tile) * 32 + lane] = make_uint4(p[0].x, p[1].x, p[0].y, p[1].y);
   }
 }
 
-__global__ void scatter_pair_kernel(const uint2* __restrict__ y, const long long* __restrict__ perm,
-                                    double2* __restrict__ u, long long Nv, int R) {
-  const long long total = Nv * R;
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const long long p = idx / R;
-    const int r = (int)(idx % R);
-    const uint2 v = y[idx];
-    const double re = (double)__uint_as_float(v.x << 16) + (double)__uint_as_float(v.y << 16);
-    const double im = (double)__uint_as_float(v.x & 0xffff0000u) + (double)__uint_as_float(v.y & 0xffff0000u);
-    u[(size_t)r * Nv + perm[p]] = make_double2(re, im);
+void nat_convert(const double2* F64, const std::vector<NatBlock>& blocks, uint4* out, cudaStream_t st) {
+  if (blocks.empty()) return;
+  NatBlock* d = upload(blocks, st);
+  for (size_t b0 = 0; b0 < blocks.size(); b0 += (1u << 30)) {
+    const unsigned n = (unsigned)std::min<size_t>(blocks.size() - b0, 1u << 30);
+    nat_convert_kernel<<<n, 128, 0, st>>>(F64, d + b0, out);
+    HB_CHECK_LAUNCH();
+  }
+  HB_CUDA(cudaStreamSynchronize(st));
+  dev_free(d);
+}
+
+// Vector word w of tile (row tile rt, m-tile mt): lane = w >> 2, j = w & 3,
+// row 8 rt + 2 (lane & 3) + (j >> 1), right-hand side 16 mt + (lane >> 2) + 8 (j & 1).
+__device__ __forceinline__ void word_coords(long long q, int MT, long long& rt, int& mt, int& w, long long& row,
+                                            int& rhs) {
+  w = (int)(q & 127);
+  const long long tm = q >> 7;
+  rt = tm / MT;
+  mt = (int)(tm - rt * MT);
+  const int ln = w >> 2, j = w & 3;
+  row = 8 * rt + 2 * (ln & 3) + (j >> 1);
+  rhs = 16 * mt + (ln >> 2) + 8 * (j & 1);
+}
+
+// x (native) = pair(scale * s[rhs * Nv + natural index of the padded row])
+__global__ void gather_native_kernel(const double2* __restrict__ s, const long long* __restrict__ pperm,
+                                     uint32_t* __restrict__ x, long long nv_tiles, long long Nv, int R, int MT,
+                                     double scale) {
+  const long long total = nv_tiles * MT * 128;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+       q += (long long)gridDim.x * blockDim.x) {
+    long long rt, row;
+    int mt, w, rhs;
+    word_coords(q, MT, rt, mt, w, row, rhs);
+    const long long nat = pperm[row];
+    double2 v = make_double2(0.0, 0.0);
+    if (nat >= 0 && rhs < R) v = s[(size_t)rhs * Nv + nat];
+    const uint2 p = to_pair((float)(v.x * scale), (float)(v.y * scale));
+    uint32_t* tile = x + (rt * MT + mt) * 256;
+    tile[w] = p.x;
+    tile[128 + w] = p.y;
   }
 }
 
-void convert_f64_pairs(const double2* a, uint2* b, long long n, cudaStream_t st) {
-  if (n <= 0) return;
-  f64_to_pair_kernel<<<1216, 256, 0, st>>>(a, b, n);
+__global__ void scatter_native_kernel(const uint32_t* __restrict__ y, const long long* __restrict__ pperm,
+                                      double2* __restrict__ u, long long nv_tiles, long long Nv, int R, int MT) {
+  const long long total = nv_tiles * MT * 128;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+       q += (long long)gridDim.x * blockDim.x) {
+    long long rt, row;
+    int mt, w, rhs;
+    word_coords(q, MT, rt, mt, w, row, rhs);
+    const long long nat = pperm[row];
+    if (nat < 0 || rhs >= R) continue;
+    const uint32_t* tile = y + (rt * MT + mt) * 256;
+    const uint32_t hi = tile[w], lo = tile[128 + w];
+    const double re = (double)__uint_as_float(hi << 16) + (double)__uint_as_float(lo << 16);
+    const double im = (double)__uint_as_float(hi & 0xffff0000u) + (double)__uint_as_float(lo & 0xffff0000u);
+    u[(size_t)rhs * Nv + nat] = make_double2(re, im);
+  }
+}
+
+void gather_native(const double2* s, const long long* pperm, uint4* x, long long nv_tiles, long long Nv, int R,
+                   int MT, double scale, cudaStream_t st) {
+  const long long total = nv_tiles * MT * 128;
+  const int grid = (int)std::max<long long>(1, std::min<long long>((total + 255) / 256, 152LL * 16));
+  gather_native_kernel<<<grid, 256, 0, st>>>(s, pperm, reinterpret_cast<uint32_t*>(x), nv_tiles, Nv, R, MT, scale);
   HB_CHECK_LAUNCH();
 }
 
-void gather_pairs(const double2* s, const long long* perm, uint2* x, long long Nv, int R, double scale,
-                  cudaStream_t st) {
-  const int grid = (int)std::min<long long>((Nv * R + 255) / 256, 152LL * 16);
-  gather_pair_kernel<<<grid, 256, 0, st>>>(s, perm, x, Nv, R, scale);
-  HB_CHECK_LAUNCH();
-}
-
-void scatter_pairs(const uint2* y, const long long* perm, double2* u, long long Nv, int R, cudaStream_t st) {
-  const int grid = (int)std::min<long long>((Nv * R + 255) / 256, 152LL * 16);
-  scatter_pair_kernel<<<grid, 256, 0, st>>>(y, perm, u, Nv, R);
+void scatter_native(const uint4* y, const long long* pperm, double2* u, long long nv_tiles, long long Nv, int R,
+                    int MT, cudaStream_t st) {
+  const long long total = nv_tiles * MT * 128;
+  const int grid = (int)std::max<long long>(1, std::min<long long>((total + 255) / 256, 152LL * 16));
+  scatter_native_kernel<<<grid, 256, 0, st>>>(reinterpret_cast<const uint32_t*>(y), pperm, u, nv_tiles, Nv, R,
+                                              MT);
   HB_CHECK_LAUNCH();
 }
 
@@ -459,16 +534,15 @@ struct DepthStreams {
 
 struct FlowPlan {
   std::vector<std::vector<PRec>> depth_pieces;   // pieces per depth, in issue order
-  int max_f_bytes = 16, max_x_rows = 1;
+  int max_f_tiles = 1, max_x_tiles = 1;
   int gmax = 0;
   std::vector<DepthStreams> streams;
 };
 
-// One chunk of a factor block (contiguous in the arena).
+// One chunk: ks k-steps of a block (contiguous tiles), its input row tiles.
 struct Chunk {
-  long long f_off, x_off, y_off;
-  int f_rows, f_cols, x_rows, r_out;
-  int x_buf, y_buf, conj;
+  long long f_tile, x_tile, y_tile;
+  int nt, ks, x_buf, y_buf;
 };
 
 // Greedy piece builder for one depth.
@@ -484,7 +558,7 @@ class PieceBuilder {
   }
 
   // mode 1: the chunks of one accumulating task (one output), possibly several pieces
-  void add_task(const std::vector<Chunk>& cs, long long y_off, int r_out, int y_buf) {
+  void add_task(const std::vector<Chunk>& cs) {
     if (cur_.nb > 0) emit();
     bool first = true;
     for (const Chunk& c : cs) {
@@ -494,9 +568,9 @@ class PieceBuilder {
         emit();
       }
       cur_.mode = 1;
-      cur_.y_off = y_off;
-      cur_.r_out = r_out;
-      cur_.y_buf = y_buf;
+      cur_.y_tile = c.y_tile;
+      cur_.nt = c.nt;
+      cur_.y_buf = c.y_buf;
       place(c);
     }
     cur_.first_last = (first ? 1 : 0) | 2;
@@ -507,18 +581,18 @@ class PieceBuilder {
     if (cur_.nb > 0) emit();
   }
 
-  int max_f = 16, max_x = 1;
+  int max_f = 1, max_x = 1;
 
  private:
   int find_run(const Chunk& c, bool& extend) const {
     for (int k = 0; k < cur_.nx; ++k) {
       const PXc& r = cur_.xc[k];
       if (r.buf != c.x_buf) continue;
-      if (c.x_off >= r.x_off && c.x_off + c.x_rows <= r.x_off + r.rows) {
+      if (c.x_tile >= r.x_tile && c.x_tile + c.ks <= r.x_tile + r.tiles) {
         extend = false;
         return k;
       }
-      if (c.x_off == r.x_off + r.rows) {
+      if (c.x_tile == r.x_tile + r.tiles) {
         extend = true;
         return k;
       }
@@ -528,144 +602,115 @@ class PieceBuilder {
 
   bool fits(const Chunk& c) const {
     if (cur_.nb >= PB_MAX) return false;
-    if (fbytes_ + c.f_rows * c.f_cols * 8 > F_CAP) return false;
+    if (ftiles_ + c.nt * c.ks > F_CAP_TILES) return false;
+    if (c.ks == 0) return true;
     bool extend = false;
     const int k = find_run(c, extend);
     if (k < 0 && cur_.nx >= PX_MAX) return false;
-    const int add = (k < 0 || extend) ? c.x_rows : 0;
-    return xrows_ + add <= X_CAP_ROWS;
+    const int add = (k < 0 || extend) ? c.ks : 0;
+    return xtiles_ + add <= X_CAP_TILES;
   }
 
   void place(const Chunk& c) {
-    bool extend = false;
-    int k = find_run(c, extend);
-    if (k < 0) {
-      k = cur_.nx++;
-      cur_.xc[k].x_off = c.x_off;
-      cur_.xc[k].rows = c.x_rows;
-      cur_.xc[k].buf = c.x_buf;
-      xrows_ += c.x_rows;
-    } else if (extend) {
-      cur_.xc[k].rows += c.x_rows;
-      xrows_ += c.x_rows;
-    }
     PBlk& b = cur_.blk[cur_.nb++];
-    b.f_off = c.f_off;
-    b.y_off = c.y_off;
-    b.f_rows = c.f_rows;
-    b.f_cols = c.f_cols;
-    b.xc = (short)k;
-    b.x_row = (short)(c.x_off - cur_.xc[k].x_off);
-    b.r_out = (short)c.r_out;
-    b.conj_t = (unsigned char)c.conj;
-    b.y_buf = (unsigned char)c.y_buf;
-    fbytes_ += c.f_rows * c.f_cols * 8;
+    b.f_tile = c.f_tile;
+    b.y_tile = c.y_tile;
+    b.nt = c.nt;
+    b.ks = c.ks;
+    b.y_buf = c.y_buf;
+    b.xc = -1;
+    b.x_t = 0;
+    if (c.ks > 0) {
+      bool extend = false;
+      int k = find_run(c, extend);
+      if (k < 0) {
+        k = cur_.nx++;
+        cur_.xc[k].x_tile = c.x_tile;
+        cur_.xc[k].tiles = c.ks;
+        cur_.xc[k].buf = c.x_buf;
+        xtiles_ += c.ks;
+      } else if (extend) {
+        cur_.xc[k].tiles += c.ks;
+        xtiles_ += c.ks;
+      }
+      b.xc = (short)k;
+      b.x_t = (short)(c.x_tile - cur_.xc[k].x_tile);
+    }
+    ftiles_ += c.nt * c.ks;
   }
 
   void emit() {
-    max_f = std::max(max_f, fbytes_);
-    max_x = std::max(max_x, xrows_);
+    max_f = std::max(max_f, ftiles_);
+    max_x = std::max(max_x, xtiles_);
     out_.push_back(cur_);
     reset();
   }
 
   void reset() {
     std::memset(&cur_, 0, sizeof(cur_));
-    fbytes_ = 0;
-    xrows_ = 0;
+    ftiles_ = 0;
+    xtiles_ = 0;
   }
 
   std::vector<PRec>& out_;
   PRec cur_;
-  int fbytes_ = 0, xrows_ = 0;
+  int ftiles_ = 0, xtiles_ = 0;
 };
 
-// Cut one logical task into chunks.  Forward: column chunks of <= kc inputs
-// (one accumulating task unless it is a single chunk).  ^H: column chunks
-// of <= oc outputs of the stored blocks; with one term every chunk is an
-// independent product.
-static void task_chunks(const FlowTask& L, std::vector<std::vector<Chunk>>& groups, bool& independent) {
-  const bool conj = !L.terms.empty() && L.terms[0].conj_t;
-  groups.clear();
-  if (!conj) {
-    if (L.r_out > MAX_OUT) throw Error{HB_ERR_UNSUPPORTED, "a factor block has more than 256 rows"};
-    const int kc = std::max(2, std::min(X_CAP_ROWS / 2, (F_CAP / 2 / (8 * std::max(1, L.r_out))) & ~1));
-    std::vector<Chunk> cs;
-    for (const FlowTerm& tm : L.terms)
-      for (int j0 = 0; j0 < tm.r_in; j0 += kc) {
-        Chunk c{};
-        c.f_off = tm.f_off + (long long)j0 * tm.f_rows;
-        c.f_rows = tm.f_rows;
-        c.f_cols = std::min(kc, tm.r_in - j0);
-        c.x_off = tm.x_off + j0;
-        c.x_rows = c.f_cols;
-        c.x_buf = tm.x_buf;
-        c.conj = 0;
-        c.r_out = L.r_out;
-        c.y_off = L.y_off;
-        c.y_buf = L.y_buf;
-        cs.push_back(c);
-      }
-    independent = (cs.size() == 1);
-    groups.push_back(cs);
-  } else {
-    int rmax = 1;
-    for (const FlowTerm& tm : L.terms) rmax = std::max(rmax, tm.r_in);
-    if (rmax > X_CAP_ROWS) throw Error{HB_ERR_UNSUPPORTED, "an adjoint factor block has too many rows"};
-    const int oc = std::min(MAX_OUT, std::max(8, (F_CAP / 2 / (8 * rmax)) & ~7));
-    independent = (L.terms.size() == 1);
-    for (int n0 = 0; n0 < L.r_out; n0 += oc) {
-      std::vector<Chunk> cs;
-      const int w = std::min(oc, L.r_out - n0);
-      for (const FlowTerm& tm : L.terms) {
-        Chunk c{};
-        c.f_off = tm.f_off + (long long)n0 * tm.f_rows;
-        c.f_rows = tm.f_rows;
-        c.f_cols = w;
-        c.x_off = tm.x_off;
-        c.x_rows = tm.r_in;
-        c.x_buf = tm.x_buf;
-        c.conj = 1;
-        c.r_out = w;
-        c.y_off = L.y_off + n0;
-        c.y_buf = L.y_buf;
-        cs.push_back(c);
-      }
-      groups.push_back(cs);
+// Cut one task into chunks of at most kc k-steps (kc nt tiles fit a piece).
+// A task that is one chunk is an independent product.
+static void task_chunks(const NatTask& L, std::vector<Chunk>& cs) {
+  if (L.nt > MAX_NT) throw Error{HB_ERR_UNSUPPORTED, "a factor block has more than 256 rows"};
+  const int kc = std::max(1, std::min(X_CAP_TILES, F_CAP_TILES / L.nt));
+  cs.clear();
+  for (const NatTerm& tm : L.terms)
+    for (int k0 = 0; k0 < tm.ks; k0 += kc) {
+      Chunk c{};
+      c.f_tile = tm.f_tile + (long long)k0 * L.nt;
+      c.x_tile = tm.x_tile + k0;
+      c.y_tile = L.y_tile;
+      c.nt = L.nt;
+      c.ks = std::min(kc, tm.ks - k0);
+      c.x_buf = tm.x_buf;
+      c.y_buf = L.y_buf;
+      cs.push_back(c);
     }
+  if (cs.empty()) {   // every input is empty: the output is zero
+    Chunk c{};
+    c.y_tile = L.y_tile;
+    c.nt = L.nt;
+    c.y_buf = L.y_buf;
+    cs.push_back(c);
   }
 }
 
-void flow_plan_build(const std::vector<FlowTask>& lt, void** plan_out) {
+void flow_plan_build(const std::vector<NatTask>& lt, void** plan_out) {
   FlowPlan* P = new FlowPlan();
   try {
     int maxd = -1;
-    for (const FlowTask& L : lt) maxd = std::max(maxd, L.depth);
+    for (const NatTask& L : lt) maxd = std::max(maxd, L.depth);
     P->depth_pieces.assign((size_t)(maxd + 1), {});
-    std::vector<std::vector<Chunk>> groups;
+    std::vector<Chunk> cs;
     for (int d = 0; d <= maxd; ++d) {
       std::vector<Chunk> indep;
       std::vector<std::vector<Chunk>> accum;
-      for (const FlowTask& L : lt) {
-        if (L.depth != d) continue;
-        bool ind = false;
-        task_chunks(L, groups, ind);
-        for (auto& cs : groups) {
-          if (ind && cs.size() == 1) indep.push_back(cs[0]);
-          else accum.push_back(cs);
-        }
+      for (const NatTask& L : lt) {
+        if (L.depth != d || L.nt == 0) continue;
+        task_chunks(L, cs);
+        if (cs.size() == 1) indep.push_back(cs[0]);
+        else accum.push_back(cs);
       }
-      // chunks that read the same or neighbouring input rows meet in one piece
+      // chunks that read the same or neighbouring input tiles meet in one piece
       std::stable_sort(indep.begin(), indep.end(), [](const Chunk& a, const Chunk& b) {
         if (a.x_buf != b.x_buf) return a.x_buf < b.x_buf;
-        return a.x_off < b.x_off;
+        return a.x_tile < b.x_tile;
       });
       PieceBuilder pb(P->depth_pieces[(size_t)d]);
       for (const Chunk& c : indep) pb.add_independent(c);
       pb.flush();
-      for (const auto& cs : accum) pb.add_task(cs, cs[0].y_off, cs[0].r_out, cs[0].y_buf);
-      P->max_f_bytes = std::max(P->max_f_bytes, pb.max_f);
-      P->max_x_rows = std::max(P->max_x_rows, pb.max_x);
+      for (const auto& ch : accum) pb.add_task(ch);
+      P->max_f_tiles = std::max(P->max_f_tiles, pb.max_f);
+      P->max_x_tiles = std::max(P->max_x_tiles, pb.max_x);
     }
   } catch (...) {
     delete P;
@@ -721,17 +766,22 @@ static void build_streams(FlowPlan* P, int gmax) {
 }
 
 template <int MT>
-static void launch_depths(FlowPlan* P, const uint2* F, uint2* x, uint2* y, uint2* xh, int R, int* err,
-                          long long budget, cudaStream_t st, const std::function<void(int, bool)>& timer) {
-  // stage: every factor chunk and input run rounded up to 16 and placed 128-byte
-  // aligned (at most 143 bytes of slack each), runs with a head pad below 16 bytes
-  const int stage = (P->max_f_bytes + P->max_x_rows * R * 8 + (PB_MAX + PX_MAX) * 160 + 127) & ~127;
-  const size_t smem = (size_t)FLOW_STAGES * stage;
+static void launch_depths(FlowPlan* P, const uint4* F, uint4* x, uint4* y, uint4* xh, int* err, long long budget,
+                          cudaStream_t st, const std::function<void(int, bool)>& timer) {
   auto k = bf_step_kernel<MT>;
-  HB_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int dev = 0, nsm = 0, per_sm = 0;
+  int dev = 0, nsm = 0, optin = 0;
   HB_CUDA(cudaGetDevice(&dev));
   HB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  HB_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  cudaFuncAttributes fa{};
+  HB_CUDA(cudaFuncGetAttributes(&fa, k));
+  const int stage = P->max_f_tiles * 512 + P->max_x_tiles * MT * 1024;
+  const int avail = optin - (int)fa.sharedSizeBytes;
+  const int stages = std::min(MAX_STAGES, avail / stage);
+  if (stages < 2) throw Error{HB_ERR_UNSUPPORTED, "step kernel stages do not fit in shared memory"};
+  const size_t smem = (size_t)stages * stage;
+  HB_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
   HB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, (NCW + 1) * 32, smem));
   if (per_sm < 1) throw Error{HB_ERR_UNSUPPORTED, "step kernel does not fit on an SM"};
   if (P->gmax != nsm * per_sm) build_streams(P, nsm * per_sm);
@@ -739,7 +789,7 @@ static void launch_depths(FlowPlan* P, const uint2* F, uint2* x, uint2* y, uint2
   for (int d = 0; d < nd; ++d) {
     const DepthStreams& ds = P->streams[(size_t)d];
     if (ds.grid == 0) continue;
-    StepArgs args{ds.d_recs, ds.d_off, F, x, y, xh, R, stage, budget, err};
+    StepArgs args{ds.d_recs, ds.d_off, F, x, y, xh, stages, stage, budget, err};
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(ds.grid);
     cfg.blockDim = dim3((NCW + 1) * 32);
@@ -756,14 +806,13 @@ static void launch_depths(FlowPlan* P, const uint2* F, uint2* x, uint2* y, uint2
   }
 }
 
-void flow_launch(void* plan, const uint2* F, uint2* x, uint2* y, uint2* xh, int R, int* err,
+void flow_launch(void* plan, const uint4* F, uint4* x, uint4* y, uint4* xh, int MT, int* err,
                  long long budget_cycles, cudaStream_t st, const std::function<void(int, bool)>& timer) {
   FlowPlan* P = static_cast<FlowPlan*>(plan);
   if (P->depth_pieces.empty()) return;
-  if (R <= 16) launch_depths<1>(P, F, x, y, xh, R, err, budget_cycles, st, timer);
-  else if (R <= 32) launch_depths<2>(P, F, x, y, xh, R, err, budget_cycles, st, timer);
-  else if (R <= 64) launch_depths<4>(P, F, x, y, xh, R, err, budget_cycles, st, timer);
-  else throw Error{HB_ERR_UNSUPPORTED, "the mixed apply takes at most 64 right-hand sides per pass"};
+  if (MT == 1) launch_depths<1>(P, F, x, y, xh, err, budget_cycles, st, timer);
+  else if (MT == 2) launch_depths<2>(P, F, x, y, xh, err, budget_cycles, st, timer);
+  else throw Error{HB_ERR_UNSUPPORTED, "the mixed apply takes 1 or 2 m-tiles of 16 right-hand sides per pass"};
 }
 
 }  // namespace hb

@@ -40,6 +40,7 @@ struct BlockRec {
   int ncols = 0;
   long long f_off = -1;
   long long xh_off = -1;
+  long long xh_tile = -1;        // native layout: first padded row tile
   std::vector<long long> skel;   // tree positions, pivot order
 };
 
@@ -296,20 +297,19 @@ void build(hb_ctx* c) {
   }
   HB_CUDA(cudaStreamSynchronize(st));
   for (const Segment& s : segs) dev_free(s.ptr);
-  c->d_pairs = dev_alloc<uint2>((size_t)nfac + 16);
-  HB_CUDA(cudaMemset(c->d_pairs, 0, sizeof(uint2) * ((size_t)nfac + 16)));
-  convert_f64_pairs(c->d_f64, c->d_pairs, nfac, st);
-  HB_CUDA(cudaStreamSynchronize(st));
 
-  // xh offsets
-  long long xh = 0;
+  // xh offsets (FP64 path: packed rows; native layout: padded row tiles)
+  long long xh = 0, xht = 0;
   for (auto& b : bfs)
     for (int k = 0; k <= b.L; ++k)
       for (auto& br : b.lev[k]) {
         br.xh_off = xh;
         xh += br.rank;
+        br.xh_tile = xht;
+        xht += (br.rank + 7) / 8;
       }
   c->xh_rows = xh;
+  c->xh_tiles = xht;
 
   // task plans
   for (int dir = 0; dir < 2; ++dir) {
@@ -445,24 +445,23 @@ void build(hb_ctx* c) {
     c->d_tasks[dir] = upload(c->tasks_h[dir]);
   }
 
-  // dataflow plans of the mixed apply (one persistent launch per apply)
+  // native arenas and plans of the mixed apply
   {
-    // logical-task id of the producer of every block, per direction
-    std::vector<std::vector<std::vector<int>>> prod((size_t)bfs.size());
-    auto leaf_term = [&](long long t, int conj) {
-      FlowTerm ft{};
-      const long long p0 = node_lo(c, Lv, t);
-      const int sz = (int)(node_hi(c, Lv, t) - p0);
-      ft.f_off = leaf_off[(size_t)t];
-      ft.x_off = p0;
-      ft.r_in = sz;
-      ft.f_rows = sz;
-      ft.producer[0] = ft.producer[1] = -1;
-      ft.x_buf = 0;
-      ft.conj_t = (unsigned char)conj;
-      return ft;
-    };
-    // butterfly index of (HODBF level l, node oi as the row set)
+    auto tiles8 = [](long long r) { return (r + 7) / 8; };
+    const long long nleaf = 1LL << Lv;
+    c->leaf_tile.assign((size_t)nleaf + 1, 0);
+    for (long long t = 0; t < nleaf; ++t)
+      c->leaf_tile[(size_t)t + 1] = c->leaf_tile[(size_t)t] + tiles8(node_hi(c, Lv, t) - node_lo(c, Lv, t));
+    c->nv_tiles = c->leaf_tile[(size_t)nleaf];
+    {
+      std::vector<long long> pp((size_t)c->nv_tiles * 8, -1);
+      for (long long t = 0; t < nleaf; ++t)
+        for (long long p = node_lo(c, Lv, t); p < node_hi(c, Lv, t); ++p)
+          pp[(size_t)(c->leaf_tile[(size_t)t] * 8 + (p - node_lo(c, Lv, t)))] = c->perm[(size_t)p];
+      c->d_pperm = upload(pp);
+    }
+    auto leaf_size = [&](long long t) { return (int)(node_hi(c, Lv, t) - node_lo(c, Lv, t)); };
+    // butterfly index of (HODBF level l, node oi as the row set / si as the column set)
     auto bf_of_o = [&](int l, long long oi) { return (int)(((1LL << (l - 1)) - 1) * 2 + (oi >> 1) * 2 + (oi & 1)); };
     auto bf_of_s = [&](int l, long long si) {
       const long long p = si >> 1;
@@ -470,164 +469,135 @@ void build(hb_ctx* c) {
       return (int)(((1LL << (l - 1)) - 1) * 2 + p * 2 + d);
     };
     for (int dir = 0; dir < 2; ++dir) {
-      std::vector<FlowTask> ft;
-      for (size_t b = 0; b < bfs.size(); ++b) {
-        prod[b].assign(bfs[b].L + 1, {});
-        for (int k = 0; k <= bfs[b].L; ++k) prod[b][k].assign(bfs[b].lev[k].size(), -1);
-      }
+      std::vector<NatBlock> nb;
+      long long ntile = 0;
+      // a native block of op(F) with outputs (r1 | r2) and inputs (k1 | k2)
+      auto nat = [&](long long src, int ld, int r1, int r2, int k1, int k2) {
+        NatBlock B{};
+        B.src_off = src;
+        B.tile0 = ntile;
+        B.ld = ld;
+        B.conj = dir;
+        B.r1 = r1;
+        B.r2 = r2;
+        B.k1 = k1;
+        B.k2 = k2;
+        ntile += (tiles8(r1) + tiles8(r2)) * (tiles8(k1) + tiles8(k2));
+        nb.push_back(B);
+        return B.tile0;
+      };
+      auto term = [](long long f_tile, long long x_tile, long long ks, int x_buf) {
+        NatTerm tm{};
+        tm.f_tile = f_tile;
+        tm.x_tile = x_tile;
+        tm.ks = (int)ks;
+        tm.x_buf = x_buf;
+        return tm;
+      };
+      std::vector<NatTask> nt;
+      auto task = [&](long long y_tile, long long ntl, int depth, int y_buf) {
+        NatTask t;
+        t.y_tile = y_tile;
+        t.nt = (int)ntl;
+        t.depth = depth;
+        t.y_buf = y_buf;
+        return t;
+      };
       if (dir == 0) {
+        // depth k: V^0 (k = 0) and W^k of every butterfly with L >= k
         for (int k = 0; k <= Lmax; ++k)
           for (size_t bi = 0; bi < bfs.size(); ++bi) {
-            Butterfly& b = bfs[bi];
+            const Butterfly& b = bfs[bi];
             if (b.L < k) continue;
             const int w = 1 << (b.L - k);
             for (int i = 0; i < (1 << k); ++i)
               for (int j = 0; j < w; ++j) {
-                BlockRec& br = b.lev[k][(size_t)i * w + j];
-                FlowTask t;
-                t.y_off = br.xh_off;
-                t.r_out = br.rank;
-                t.depth = k;
-                t.y_buf = 2;
-                FlowTerm tm{};
-                tm.f_off = br.f_off;
-                tm.f_rows = br.rank;
-                tm.conj_t = 0;
+                const BlockRec& br = b.lev[k][(size_t)i * w + j];
+                NatTask t = task(br.xh_tile, tiles8(br.rank), k, 2);
                 if (k == 0) {
-                  const long long n0 = node_lo(c, b.l + b.L, ((long long)b.si << b.L) + j);
-                  tm.x_off = n0;
-                  tm.r_in = (int)(node_hi(c, b.l + b.L, ((long long)b.si << b.L) + j) - n0);
-                  tm.x_buf = 0;
-                  tm.producer[0] = tm.producer[1] = -1;
+                  const long long leaf = ((long long)b.si << b.L) + j;
+                  const int nn = leaf_size(leaf);
+                  t.terms.push_back(term(nat(br.f_off, br.rank, br.rank, 0, nn, 0), c->leaf_tile[(size_t)leaf],
+                                         tiles8(nn), 0));
                 } else {
                   const size_t q1 = (size_t)(i / 2) * (2 * w) + 2 * j;
                   const BlockRec& c1 = b.lev[k - 1][q1];
                   const BlockRec& c2 = b.lev[k - 1][q1 + 1];
-                  tm.x_off = c1.xh_off;
-                  tm.r_in = c1.rank + c2.rank;
-                  tm.x_buf = 2;
-                  tm.producer[0] = prod[bi][k - 1][q1];
-                  tm.producer[1] = prod[bi][k - 1][q1 + 1];
+                  t.terms.push_back(term(nat(br.f_off, br.rank, br.rank, 0, c1.rank, c2.rank), c1.xh_tile,
+                                         tiles8(c1.rank) + tiles8(c2.rank), 2));
                 }
-                t.terms.push_back(tm);
-                prod[bi][k][(size_t)i * w + j] = (int)ft.size();
-                ft.push_back(std::move(t));
+                nt.push_back(std::move(t));
               }
           }
-        for (long long t = 0; t < (1LL << Lv); ++t) {
-          FlowTask o;
-          o.y_off = node_lo(c, Lv, t);
-          o.r_out = (int)(node_hi(c, Lv, t) - o.y_off);
-          o.depth = Lmax + 1;
-          o.y_buf = 1;
-          o.terms.push_back(leaf_term(t, 0));
+        // last depth: y(leaf t) = D_t x(t) + sum over levels of K^L x_hat
+        for (long long t = 0; t < nleaf; ++t) {
+          const int sz = leaf_size(t);
+          NatTask o = task(c->leaf_tile[(size_t)t], tiles8(sz), Lmax + 1, 1);
+          o.terms.push_back(term(nat(leaf_off[(size_t)t], sz, sz, 0, sz, 0), c->leaf_tile[(size_t)t], tiles8(sz), 0));
           for (int l = 1; l <= Lv; ++l) {
             const long long oi = t >> (Lv - l);
-            const int bi = bf_of_o(l, oi);
-            const Butterfly& b = bfs[(size_t)bi];
+            const Butterfly& b = bfs[(size_t)bf_of_o(l, oi)];
             const long long i = t - (oi << b.L);
             const BlockRec& br = b.lev[b.L][(size_t)i];
-            FlowTerm tm{};
-            tm.f_off = b.kl_off[(size_t)i];
-            tm.f_rows = o.r_out;
-            tm.x_off = br.xh_off;
-            tm.r_in = br.rank;
-            tm.x_buf = 2;
-            tm.producer[0] = prod[(size_t)bi][b.L][(size_t)i];
-            tm.producer[1] = -1;
-            o.terms.push_back(tm);
+            o.terms.push_back(term(nat(b.kl_off[(size_t)i], sz, sz, 0, br.rank, 0), br.xh_tile, tiles8(br.rank), 2));
           }
-          ft.push_back(std::move(o));
+          nt.push_back(std::move(o));
         }
       } else {
         // depth 0: K^L^H
         for (size_t bi = 0; bi < bfs.size(); ++bi) {
-          Butterfly& b = bfs[bi];
+          const Butterfly& b = bfs[bi];
           for (int i = 0; i < (1 << b.L); ++i) {
-            BlockRec& br = b.lev[b.L][(size_t)i];
-            const long long t0 = node_lo(c, b.l + b.L, ((long long)b.oi << b.L) + i);
-            const int sz = (int)(node_hi(c, b.l + b.L, ((long long)b.oi << b.L) + i) - t0);
-            FlowTask t;
-            t.y_off = br.xh_off;
-            t.r_out = br.rank;
-            t.depth = 0;
-            t.y_buf = 2;
-            FlowTerm tm{};
-            tm.f_off = b.kl_off[(size_t)i];
-            tm.f_rows = sz;
-            tm.x_off = t0;
-            tm.r_in = sz;
-            tm.x_buf = 0;
-            tm.conj_t = 1;
-            tm.producer[0] = tm.producer[1] = -1;
-            t.terms.push_back(tm);
-            prod[bi][b.L][(size_t)i] = (int)ft.size();
-            ft.push_back(std::move(t));
+            const BlockRec& br = b.lev[b.L][(size_t)i];
+            const long long leaf = ((long long)b.oi << b.L) + i;
+            const int sz = leaf_size(leaf);
+            NatTask t = task(br.xh_tile, tiles8(br.rank), 0, 2);
+            t.terms.push_back(term(nat(b.kl_off[(size_t)i], sz, br.rank, 0, sz, 0), c->leaf_tile[(size_t)leaf],
+                                   tiles8(sz), 0));
+            nt.push_back(std::move(t));
           }
         }
-        // depth d: W^{L-d+1}^H, producing the pair of level L-d blocks
+        // depth d: W^{L-d+1}^H, writing the pair of level L-d blocks
         for (int d = 1; d <= Lmax; ++d)
           for (size_t bi = 0; bi < bfs.size(); ++bi) {
-            Butterfly& b = bfs[bi];
+            const Butterfly& b = bfs[bi];
             if (b.L < d) continue;
-            const int t = b.L - d + 1;
-            const int w = 1 << (b.L - t);
-            for (int p = 0; p < (1 << (t - 1)); ++p)
+            const int tl = b.L - d + 1;
+            const int w = 1 << (b.L - tl);
+            for (int p = 0; p < (1 << (tl - 1)); ++p)
               for (int j = 0; j < w; ++j) {
                 const size_t q1 = (size_t)p * (2 * w) + 2 * j;
-                BlockRec& o1 = b.lev[t - 1][q1];
-                BlockRec& o2 = b.lev[t - 1][q1 + 1];
-                FlowTask tk;
-                tk.y_off = o1.xh_off;
-                tk.r_out = o1.rank + o2.rank;
-                tk.depth = d;
-                tk.y_buf = 2;
+                const BlockRec& o1 = b.lev[tl - 1][q1];
+                const BlockRec& o2 = b.lev[tl - 1][q1 + 1];
+                NatTask t = task(o1.xh_tile, tiles8(o1.rank) + tiles8(o2.rank), d, 2);
                 for (int cc = 0; cc < 2; ++cc) {
-                  const size_t qb = (size_t)(2 * p + cc) * w + j;
-                  const BlockRec& br = b.lev[t][qb];
-                  FlowTerm tm{};
-                  tm.f_off = br.f_off;
-                  tm.f_rows = br.rank;
-                  tm.x_off = br.xh_off;
-                  tm.r_in = br.rank;
-                  tm.x_buf = 2;
-                  tm.conj_t = 1;
-                  tm.producer[0] = prod[bi][t][qb];
-                  tm.producer[1] = -1;
-                  tk.terms.push_back(tm);
+                  const BlockRec& br = b.lev[tl][(size_t)(2 * p + cc) * w + j];
+                  t.terms.push_back(term(nat(br.f_off, br.rank, o1.rank, o2.rank, br.rank, 0), br.xh_tile,
+                                         tiles8(br.rank), 2));
                 }
-                prod[bi][t - 1][q1] = prod[bi][t - 1][q1 + 1] = (int)ft.size();
-                ft.push_back(std::move(tk));
+                nt.push_back(std::move(t));
               }
           }
-        for (long long t = 0; t < (1LL << Lv); ++t) {
-          FlowTask o;
-          o.y_off = node_lo(c, Lv, t);
-          o.r_out = (int)(node_hi(c, Lv, t) - o.y_off);
-          o.depth = Lmax + 1;
-          o.y_buf = 1;
-          o.terms.push_back(leaf_term(t, 1));
+        // last depth: y(leaf t) = D_t^H x(t) + sum over levels of V^0^H x_hat
+        for (long long t = 0; t < nleaf; ++t) {
+          const int sz = leaf_size(t);
+          NatTask o = task(c->leaf_tile[(size_t)t], tiles8(sz), Lmax + 1, 1);
+          o.terms.push_back(term(nat(leaf_off[(size_t)t], sz, sz, 0, sz, 0), c->leaf_tile[(size_t)t], tiles8(sz), 0));
           for (int l = 1; l <= Lv; ++l) {
             const long long si = t >> (Lv - l);
-            const int bi = bf_of_s(l, si);
-            const Butterfly& b = bfs[(size_t)bi];
+            const Butterfly& b = bfs[(size_t)bf_of_s(l, si)];
             const long long j = t - (si << b.L);
             const BlockRec& br = b.lev[0][(size_t)j];
-            FlowTerm tm{};
-            tm.f_off = br.f_off;
-            tm.f_rows = br.rank;
-            tm.x_off = br.xh_off;
-            tm.r_in = br.rank;
-            tm.x_buf = 2;
-            tm.conj_t = 1;
-            tm.producer[0] = prod[(size_t)bi][0][(size_t)j];
-            tm.producer[1] = -1;
-            o.terms.push_back(tm);
+            o.terms.push_back(term(nat(br.f_off, br.rank, sz, 0, br.rank, 0), br.xh_tile, tiles8(br.rank), 2));
           }
-          ft.push_back(std::move(o));
+          nt.push_back(std::move(o));
         }
       }
-      flow_plan_build(ft, &c->flow_plan[dir]);
+      c->nat_tiles[dir] = ntile;
+      c->d_nat[dir] = dev_alloc<uint4>((size_t)std::max<long long>(ntile, 1) * 32);
+      nat_convert(c->d_f64, nb, c->d_nat[dir], st);
+      HB_CUDA(cudaStreamSynchronize(st));
+      flow_plan_build(nt, &c->flow_plan[dir]);
     }
   }
   HB_CUDA(cudaDeviceSynchronize());
@@ -636,7 +606,7 @@ void build(hb_ctx* c) {
   c->stats.max_rank = max_rank;
   c->stats.factor_entries = nfac;
   c->stats.factor_bytes_fp64 = nfac * (long long)sizeof(double2);
-  c->stats.factor_bytes_mixed = nfac * (long long)sizeof(float2);
+  c->stats.factor_bytes_mixed = c->nat_tiles[0] * 512;
   c->stats.id_blocks = id_blocks;
   c->stats.sampled_entries = sampled;
   c->stats.skeleton_rows = c->xh_rows;

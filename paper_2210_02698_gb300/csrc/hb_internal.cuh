@@ -95,24 +95,35 @@ struct Task {
   unsigned char conj_t, kind, pad0, pad1;
 };
 
-// Dataflow plan of the mixed apply (one persistent launch): a logical task
-// writes y_off .. y_off + r_out of buffer y_buf as the sum of its terms
-// op(F) X; a term's input rows were written by up to two earlier logical
-// tasks (`producer`, -1 = none).  Tasks are listed in dependency order.
-struct FlowTerm {
-  long long f_off;   // factor block start (element offset)
-  long long x_off;   // first input row
-  int r_in;          // input rows
-  int f_rows;        // stored rows of the block (r_out when !conj_t, r_in when conj_t)
-  int producer[2];
-  unsigned char x_buf, conj_t;
+// Native (MMA-fragment) layout of the mixed apply (bf_mma.cu).  A factor
+// block op(F) (outputs x inputs) is stored as tiles of 8 outputs x 8 inputs
+// (512 bytes), ordered [k-step][n-tile]; rows of a block part are padded to
+// a multiple of 8 with zeros.  NatBlock says where a native block comes
+// from: the column-major FP64 block at src_off (leading dimension ld), op =
+// identity or conjugate transpose, outputs in one or two parts (r1, r2) and
+// inputs in one or two parts (k1, k2), each part padded on its own.
+struct NatBlock {
+  long long src_off;
+  long long tile0;       // first tile in the native arena
+  int ld, conj;
+  int r1, r2, k1, k2;
 };
-struct FlowTask {
-  long long y_off;
-  int r_out;
-  int depth;          // dependency depth: inputs come from tasks of smaller depth only
-  unsigned char y_buf;
-  std::vector<FlowTerm> terms;
+// One term of a native task: ks k-steps of the block at f_tile, input row
+// tiles x_tile .. x_tile + ks of buffer x_buf (0 = x, 1 = y, 2 = xh).
+struct NatTerm {
+  long long f_tile;
+  long long x_tile;
+  int ks;
+  int x_buf;
+};
+// A task writes nt row tiles of buffer y_buf from y_tile on as the sum of
+// its terms; depth d reads only what depths < d wrote.
+struct NatTask {
+  long long y_tile;
+  int nt;
+  int depth;
+  int y_buf;
+  std::vector<NatTerm> terms;
 };
 
 // Host-side batch of ragged entry blocks (entries.cu).
@@ -157,15 +168,21 @@ struct hb_ctx {
   // build results
   bool built = false;
   hb_stats stats{};
-  // factor arenas: FP64 (double2) and split-BF16 pairs (uint2), same element offsets
+  // FP64 factor arena (double2, column-major blocks)
   long long n_factor = 0;
   double2* d_f64 = nullptr;
-  uint2* d_pairs = nullptr;
+  // native split-BF16 arenas of the mixed apply: [0] forward, [1] adjoint (512-byte tiles)
+  uint4* d_nat[2] = {nullptr, nullptr};
+  long long nat_tiles[2] = {0, 0};
+  std::vector<long long> leaf_tile;   // first padded row tile of every leaf (+ total)
+  long long nv_tiles = 0;             // row tiles of the padded tree-ordered vectors
+  long long xh_tiles = 0;             // row tiles of the padded intermediate vectors
+  long long* d_pperm = nullptr;       // padded row -> natural index (-1: padding)
   // apply plans: steps[0] forward, steps[1] adjoint; each step = task range
   std::vector<int> step_begin[2];
   std::vector<hb::Task> tasks_h[2];
   hb::Task* d_tasks[2] = {nullptr, nullptr};
-  void* flow_plan[2] = {nullptr, nullptr};  // tensor-core dataflow plans (bf_mma.cu)
+  void* flow_plan[2] = {nullptr, nullptr};  // mixed apply plans (bf_mma.cu)
   int* h_err = nullptr;                    // mapped pinned error word of bounded device waits
   int* d_err = nullptr;
   long long xh_rows = 0;
@@ -176,6 +193,10 @@ struct hb_ctx {
   void* d_x = nullptr;
   void* d_y = nullptr;
   void* d_xh = nullptr;
+  // mixed apply scratch (native layout, up to 32 right-hand sides)
+  uint4* d_mx = nullptr;
+  uint4* d_my = nullptr;
+  uint4* d_mxh = nullptr;
 
   // timing
   bool timing = false;
@@ -201,15 +222,17 @@ void emit_v(int count, const int* d_m, const int* d_n, const long long* d_aoff, 
 void build(hb_ctx* c);
 void id_batch_noalloc(int count, const int* m, const int* n, const long long* a_off, double2* A, double eps,
                       int* rank, int* skel, double2* V, cudaStream_t st);
-void flow_plan_build(const std::vector<FlowTask>& tasks, void** plan_out);
+void flow_plan_build(const std::vector<NatTask>& tasks, void** plan_out);
 void flow_plan_free(void* plan);
 int flow_plan_depths(const void* plan);
-void flow_launch(void* plan, const uint2* F, uint2* x, uint2* y, uint2* xh, int R, int* err,
+// MT = m-tiles of 16 right-hand sides (1 or 2)
+void flow_launch(void* plan, const uint4* F, uint4* x, uint4* y, uint4* xh, int MT, int* err,
                  long long budget_cycles, cudaStream_t st, const std::function<void(int, bool)>& timer);
-void convert_f64_pairs(const double2* a, uint2* b, long long n, cudaStream_t st);
-void gather_pairs(const double2* s, const long long* perm, uint2* x, long long Nv, int R, double scale,
-                  cudaStream_t st);
-void scatter_pairs(const uint2* y, const long long* perm, double2* u, long long Nv, int R, cudaStream_t st);
+void nat_convert(const double2* F64, const std::vector<NatBlock>& blocks, uint4* out, cudaStream_t st);
+void gather_native(const double2* s, const long long* pperm, uint4* x, long long nv_tiles, long long Nv, int R,
+                   int MT, double scale, cudaStream_t st);
+void scatter_native(const uint4* y, const long long* pperm, double2* u, long long nv_tiles, long long Nv, int R,
+                    int MT, cudaStream_t st);
 void apply_bf(hb_ctx* c, const double2* s, double2* u, int nrhs, int adjoint, int precision,
               cudaStream_t st);
 void tree_build(hb_ctx* c);
