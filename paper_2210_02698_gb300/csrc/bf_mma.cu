@@ -63,47 +63,70 @@
 
 namespace hb {
 
-constexpr int NCW = 8;                 // consumer warps
-constexpr int PB_MAX = 8;              // factor chunks per piece
-constexpr int PX_MAX = 8;              // input runs per piece
-constexpr int MAX_STAGES = 4;
-constexpr int F_CAP_TILES = 96;        // factor tiles (512 bytes) per piece
-constexpr int X_CAP_TILES = 24;        // input row tiles per piece
-constexpr int MAX_NT = 32;             // n-tiles of one output (256 rows)
+// Ring geometry (compile-time; the defaults are the tuned values).
+#ifndef HB_FLOW_NCW
+#define HB_FLOW_NCW 8
+#endif
+#ifndef HB_FLOW_TILES_PER_WARP
+#define HB_FLOW_TILES_PER_WARP 8
+#endif
+#ifndef HB_FLOW_F_CAP
+#define HB_FLOW_F_CAP 96
+#endif
+#ifndef HB_FLOW_X_CAP
+#define HB_FLOW_X_CAP 24
+#endif
+#ifndef HB_FLOW_MAX_STAGES
+#define HB_FLOW_MAX_STAGES 4
+#endif
+#ifndef HB_FLOW_PIECES_PER_SM
+#define HB_FLOW_PIECES_PER_SM 0
+#endif
+constexpr int NCW = HB_FLOW_NCW;                   // consumer warps
+constexpr int PB_MAX = 8;                          // factor chunks per piece
+constexpr int PX_MAX = 8;                          // input runs per piece
+constexpr int MAX_STAGES = HB_FLOW_MAX_STAGES;
+constexpr int F_CAP_TILES = HB_FLOW_F_CAP;         // factor tiles (512 bytes) per piece
+constexpr int X_CAP_TILES = HB_FLOW_X_CAP;         // input row tiles per piece
+constexpr int PIECES_PER_SM = HB_FLOW_PIECES_PER_SM;   // > 0: smaller pieces for small depths
+constexpr int MAX_NT = 32;                         // n-tiles of one output (256 rows)
 constexpr uint32_t IM_SIGN = 0x80000000u;   // sign bit of the imaginary (upper) bf16
 
-struct PBlk {            // one factor chunk of a piece (32 bytes)
-  long long f_tile;      // first factor tile
-  long long y_tile;      // mode 0: first output row tile
-  int nt;                // n-tiles of the block
-  int ks;                // k-steps of the chunk
-  short xc;              // input run (-1: none)
-  short x_t;             // first row tile inside that run
-  int y_buf;             // mode 0: output buffer
+// A piece record (1 KB); the host planner precomputes everything in it.
+// copies: one cp.async.bulk each into the stage: a factor chunk (buf 3) to
+// stage byte dst, an input run (buf 0..2 = x, y, xh) to the input region,
+// row tile dst (the input region starts at f_bytes; an input row tile is
+// MT KB).  items: consumer warp w runs items [wbeg[w], wbeg[w + 1]).
+struct PCopy {           // 16 bytes
+  long long src;         // first factor tile / first vector row tile
+  int dst;
+  int tiles_buf;         // tiles | buf << 28
 };
 
-struct PXc {             // one run of input row tiles (16 bytes)
-  long long x_tile;
-  int tiles;
-  int buf;
+struct PItem {           // 24 bytes: ks k-steps x ntl n-tiles of one block
+  long long y_tile;      // first output row tile
+  int f_soff;            // stage byte offset of the item's first factor tile
+  int x_t;               // first input row tile in the input region
+  short ks;
+  short f_stride;        // n-tiles of the block (tiles between k-steps)
+  unsigned char ntl;
+  unsigned char y_buf;
+  unsigned char flags;   // 1: zero the accumulators first, 2: store them after
+  unsigned char pad;
 };
 
-struct PRec {            // one piece, 512 bytes
-  int nb, nx, mode, first_last;
-  long long y_tile;      // mode 1 output
-  int nt, y_buf;
-  PBlk blk[PB_MAX];
-  PXc xc[PX_MAX];
-  unsigned char pad[512 - 32 - PB_MAX * 32 - PX_MAX * 16];
+constexpr int MAX_COPIES = 16, MAX_ITEMS = 30;
+struct PRec {
+  int ncopy;
+  int f_bytes;           // factor region of the stage
+  int x_tiles;           // input row tiles after it
+  int pad0;
+  unsigned char wbeg[32];
+  PCopy cp[MAX_COPIES];
+  PItem it[MAX_ITEMS];
 };
-static_assert(sizeof(PBlk) == 32, "PBlk layout");
-static_assert(sizeof(PRec) == 512, "PRec layout");
-
-struct StageMeta {
-  PRec rec;
-  int f_soff[PB_MAX];    // byte offset of each chunk in the stage
-  int x_soff[PX_MAX];    // byte offset of each run in the stage
-};
+static_assert(sizeof(PCopy) == 16 && sizeof(PItem) == 24 && sizeof(PRec) == 1024, "record layout");
+static_assert(NCW < 32 && PB_MAX + PX_MAX <= MAX_COPIES, "record capacity");
 
 // ------------------------------------------------------------ helpers ----
 __device__ __forceinline__ uint32_t bf16x2(float lo, float hi) {
@@ -189,11 +212,12 @@ struct StepArgs {
   int* err;
 };
 
-// n-tiles per warp item: 8 / MT keeps the accumulators at 64 registers
+// n-tiles per warp item (the accumulators take 8 NTW MT registers)
 template <int MT>
 struct Tiles {
-  static constexpr int NTW = 8 / MT;
+  static constexpr int NTW = HB_FLOW_TILES_PER_WARP / MT;
 };
+static_assert(NCW * HB_FLOW_TILES_PER_WARP / 2 >= MAX_NT, "an accumulating task must fit the consumer warps");
 
 // Accumulate ks k-steps of a chunk into acc: n-tiles [t0, t0 + NTL) of a
 // block with nt n-tiles (Fs: its first k-step), input tiles Xs.  NTL is a
@@ -293,7 +317,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) bf_step_kernel(StepArgs a) 
   constexpr int NTW = Tiles<MT>::NTW;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t full[MAX_STAGES], empty[MAX_STAGES];
-  __shared__ __align__(16) StageMeta meta[MAX_STAGES];
+  __shared__ __align__(16) PRec meta[MAX_STAGES];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nst = a.stages;
   auto buf = [&](int id) { return id == 0 ? a.x : (id == 1 ? a.y : a.xh); };
@@ -311,46 +335,46 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) bf_step_kernel(StepArgs a) 
 
   if (warp == NCW) {
     // ------------------------------------------------------------ producer
-    // Each record (512 bytes) is read by the warp in one coalesced load; the
-    // first pieces get their factor chunks (constant data) before the wait
-    // for the previous depth and their input runs after it.
+    // The warp loads each record (1 KB) with two coalesced loads, one lane
+    // per copy issues the copies; factor chunks (constant data) of the first
+    // piece go out before the wait for the previous depth, input runs after.
     bool waited = false;
     const int4* src = reinterpret_cast<const int4*>(a.recs + rb);
-    int4 nxt = (npc > 0) ? src[lane] : make_int4(0, 0, 0, 0);
+    int4 n0 = make_int4(0, 0, 0, 0), n1 = n0;
+    if (npc > 0) {
+      n0 = src[lane];
+      n1 = src[32 + lane];
+    }
     for (long long i = 0; i < npc; ++i) {
       const int s = (int)(i % nst);
-      const int4 cur = nxt;
-      if (i + 1 < npc) nxt = src[(i + 1) * 32 + lane];   // prefetch the next record
-      if (i >= nst) mbar_wait_until(&empty[s], (uint32_t)(((i / nst) - 1) & 1), deadline, a.err);
-      reinterpret_cast<int4*>(&meta[s].rec)[lane] = cur;
-      __syncwarp();
-      if (lane == 0) {
-        StageMeta& m = meta[s];
-        const PRec& r = m.rec;
-        unsigned char* st = smem + (size_t)s * a.stage_bytes;
-        uint32_t off = 0;
-        for (int b = 0; b < r.nb; ++b) {
-          m.f_soff[b] = (int)off;
-          off += (uint32_t)(r.blk[b].nt * r.blk[b].ks) * 512u;
-        }
-        for (int c = 0; c < r.nx; ++c) {
-          m.x_soff[c] = (int)off;
-          off += (uint32_t)r.xc[c].tiles * (uint32_t)(MT * 1024);
-        }
-        mbar_expect_tx(&full[s], off);
-        for (int b = 0; b < r.nb; ++b) {
-          const uint32_t fb = (uint32_t)(r.blk[b].nt * r.blk[b].ks) * 512u;
-          if (fb) tma_load_1d(st + m.f_soff[b], a.F + r.blk[b].f_tile * 32, fb, &full[s]);
-        }
-        if (!waited) {
-          asm volatile("griddepcontrol.wait;" ::: "memory");
-          asm volatile("fence.proxy.async.global;" ::: "memory");
-          waited = true;
-        }
-        for (int c = 0; c < r.nx; ++c)
-          tma_load_1d(st + m.x_soff[c], buf(r.xc[c].buf) + r.xc[c].x_tile * (MT * 64),
-                      (uint32_t)r.xc[c].tiles * (uint32_t)(MT * 1024), &full[s]);
+      const int4 c0 = n0, c1 = n1;
+      if (i + 1 < npc) {   // prefetch the next record
+        n0 = src[(i + 1) * 64 + lane];
+        n1 = src[(i + 1) * 64 + 32 + lane];
       }
+      if (i >= nst) mbar_wait_until(&empty[s], (uint32_t)(((i / nst) - 1) & 1), deadline, a.err);
+      int4* m = reinterpret_cast<int4*>(&meta[s]);
+      m[lane] = c0;
+      m[32 + lane] = c1;
+      __syncwarp();
+      const PRec& r = meta[s];
+      const int f_bytes = r.f_bytes;
+      if (lane == 0) mbar_expect_tx(&full[s], (uint32_t)f_bytes + (uint32_t)r.x_tiles * (uint32_t)(MT * 1024));
+      __syncwarp();
+      unsigned char* st = smem + (size_t)s * a.stage_bytes;
+      const bool mine = lane < r.ncopy;
+      PCopy c{};
+      if (mine) c = r.cp[lane];
+      const int bid = c.tiles_buf >> 28, tiles = c.tiles_buf & 0x0fffffff;
+      if (mine && bid == 3) tma_load_1d(st + c.dst, a.F + c.src * 32, (uint32_t)tiles * 512u, &full[s]);
+      if (!waited) {
+        asm volatile("griddepcontrol.wait;" ::: "memory");
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        waited = true;
+      }
+      if (mine && bid < 3)
+        tma_load_1d(st + f_bytes + (size_t)c.dst * (MT * 1024), buf(bid) + c.src * (MT * 64),
+                    (uint32_t)tiles * (uint32_t)(MT * 1024), &full[s]);
       __syncwarp();
     }
     if (lane == 0) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
@@ -359,48 +383,22 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) bf_step_kernel(StepArgs a) 
 
   // -------------------------------------------------------------- consumers
   float acc[NTW][MT][8];
+  zero_acc<MT>(acc);
   for (long long i = 0; i < npc; ++i) {
     const int s = (int)(i % nst);
     const bool ok = mbar_wait_until(&full[s], (uint32_t)((i / nst) & 1), deadline, a.err);
-    const StageMeta& m = meta[s];
-    const PRec& r = m.rec;
+    const PRec& r = meta[s];
     const unsigned char* st = smem + (size_t)s * a.stage_bytes;
-    const int nb = ok ? r.nb : 0;
-    if (r.mode == 0) {
-      // independent chunks: work items (chunk, up to ipt n-tiles) dealt to the warps
-      int total_tiles = 0;
-      for (int b = 0; b < nb; ++b) total_tiles += r.blk[b].nt;
-      const int ipt = max(1, min(NTW, (total_tiles + NCW - 1) / NCW));
-      int item = 0;
-      for (int b = 0; b < nb; ++b) {
-        const PBlk& B = r.blk[b];
-        for (int t0 = 0; t0 < B.nt; t0 += ipt, ++item) {
-          if (item % NCW != warp) continue;
-          const int ntl = min(ipt, B.nt - t0);
-          zero_acc<MT>(acc);
-          if (B.xc >= 0) {
-            const uint4* Fs = reinterpret_cast<const uint4*>(st + m.f_soff[b]);
-            const uint4* Xs = reinterpret_cast<const uint4*>(st + m.x_soff[B.xc]) + (size_t)B.x_t * MT * 64;
-            chunk_mma<MT>(Fs, Xs, B.nt, B.ks, t0, ntl, lane, acc);
-          }
-          store_tiles<MT>(buf(B.y_buf) + (size_t)B.y_tile * MT * 64, t0, ntl, lane, acc);
-        }
-      }
-    } else {
-      // every chunk accumulates into one output; warp w owns a contiguous tile range
-      const int ipt = max(1, min(NTW, (r.nt + NCW - 1) / NCW));
-      const int t0 = warp * ipt, ntl = max(0, min(ipt, r.nt - t0));
-      if (r.first_last & 1) zero_acc<MT>(acc);
-      if (ntl > 0) {
-        for (int b = 0; b < nb; ++b) {
-          const PBlk& B = r.blk[b];
-          if (B.xc < 0) continue;
-          const uint4* Fs = reinterpret_cast<const uint4*>(st + m.f_soff[b]);
-          const uint4* Xs = reinterpret_cast<const uint4*>(st + m.x_soff[B.xc]) + (size_t)B.x_t * MT * 64;
-          chunk_mma<MT>(Fs, Xs, B.nt, B.ks, t0, ntl, lane, acc);
-        }
-        if (r.first_last & 2) store_tiles<MT>(buf(r.y_buf) + (size_t)r.y_tile * MT * 64, t0, ntl, lane, acc);
-      }
+    const uint4* xr = reinterpret_cast<const uint4*>(st + r.f_bytes);
+    const int e1 = ok ? r.wbeg[warp + 1] : 0;
+    for (int e = r.wbeg[warp]; e < e1; ++e) {
+      const PItem& it = r.it[e];
+      const int flags = it.flags, ntl = it.ntl, ks = it.ks;
+      if (flags & 1) zero_acc<MT>(acc);
+      if (ks > 0)
+        chunk_mma<MT>(reinterpret_cast<const uint4*>(st + it.f_soff), xr + (size_t)it.x_t * (MT * 64), it.f_stride,
+                      ks, 0, ntl, lane, acc);
+      if (flags & 2) store_tiles<MT>(buf(it.y_buf) + (size_t)it.y_tile * (MT * 64), 0, ntl, lane, acc);
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);   // this warp is done with stage s
@@ -526,6 +524,27 @@ void scatter_native(const uint4* y, const long long* pperm, double2* u, long lon
 }
 
 // ------------------------------------------------------------- planning ----
+// One chunk: ks k-steps of a block (contiguous tiles), its input row tiles.
+struct Chunk {
+  long long f_tile, x_tile, y_tile;
+  int nt, ks, x_buf, y_buf;
+};
+
+struct Run {
+  long long x_tile;
+  int tiles, buf;
+};
+
+// A piece as the builder forms it; encoded into a PRec for a given MT when
+// the launch streams are set up.
+struct HostPiece {
+  int mode = 0, first_last = 0;
+  std::vector<Chunk> ch;
+  std::vector<int> ch_run, ch_xt;   // input run of each chunk (-1: none), first tile inside it
+  std::vector<Run> runs;
+  int ftiles = 0, xtiles = 0;
+};
+
 struct DepthStreams {
   int grid = 0;
   PRec* d_recs = nullptr;
@@ -533,44 +552,58 @@ struct DepthStreams {
 };
 
 struct FlowPlan {
-  std::vector<std::vector<PRec>> depth_pieces;   // pieces per depth, in issue order
+  std::vector<std::vector<HostPiece>> depth_pieces;   // pieces per depth, in issue order
   int max_f_tiles = 1, max_x_tiles = 1;
-  int gmax = 0;
-  std::vector<DepthStreams> streams;
+  int gmax[3] = {0, 0, 0};                            // per MT
+  std::vector<DepthStreams> streams[3];
 };
 
-// One chunk: ks k-steps of a block (contiguous tiles), its input row tiles.
-struct Chunk {
-  long long f_tile, x_tile, y_tile;
-  int nt, ks, x_buf, y_buf;
-};
+constexpr int NTW_MIN = HB_FLOW_TILES_PER_WARP / 2;   // n-tiles per item at MT = 2
+
+// n-tiles per item: mode 0 spreads the piece's n-tiles over the warps,
+// mode 1 gives warp g the n-tiles [g ipt, (g + 1) ipt) of the one output.
+static int mode0_ipt(const std::vector<Chunk>& ch, int ntw) {
+  int total = 0;
+  for (const Chunk& c : ch) total += c.nt;
+  return std::max(1, std::min(ntw, (total + NCW - 1) / NCW));
+}
+static int mode1_ipt(int nt) { return std::max(1, (nt + NCW - 1) / NCW); }
+
+static int count_items(const std::vector<Chunk>& ch, int mode, int ntw) {
+  if (ch.empty()) return 0;
+  if (mode == 0) {
+    const int ipt = mode0_ipt(ch, ntw);
+    int n = 0;
+    for (const Chunk& c : ch) n += (c.nt + ipt - 1) / ipt;
+    return n;
+  }
+  const int ipt = mode1_ipt(ch[0].nt);
+  return (int)ch.size() * ((ch[0].nt + ipt - 1) / ipt);
+}
 
 // Greedy piece builder for one depth.
 class PieceBuilder {
  public:
-  explicit PieceBuilder(std::vector<PRec>& out) : out_(out) { reset(); }
+  PieceBuilder(std::vector<HostPiece>& out, int f_cap) : out_(out), f_cap_(f_cap) {}
 
   // mode 0: an independent chunk with its own output
   void add_independent(const Chunk& c) {
-    if (cur_.nb > 0 && (cur_.mode != 0 || !fits(c))) emit();
+    if (!cur_.ch.empty() && (cur_.mode != 0 || !fits(c, 0))) emit();
     cur_.mode = 0;
     place(c);
   }
 
   // mode 1: the chunks of one accumulating task (one output), possibly several pieces
   void add_task(const std::vector<Chunk>& cs) {
-    if (cur_.nb > 0) emit();
+    if (!cur_.ch.empty()) emit();
     bool first = true;
     for (const Chunk& c : cs) {
-      if (cur_.nb > 0 && !fits(c)) {
+      if (!cur_.ch.empty() && !fits(c, 1)) {
         cur_.first_last = first ? 1 : 0;
         first = false;
         emit();
       }
       cur_.mode = 1;
-      cur_.y_tile = c.y_tile;
-      cur_.nt = c.nt;
-      cur_.y_buf = c.y_buf;
       place(c);
     }
     cur_.first_last = (first ? 1 : 0) | 2;
@@ -578,90 +611,156 @@ class PieceBuilder {
   }
 
   void flush() {
-    if (cur_.nb > 0) emit();
+    if (!cur_.ch.empty()) emit();
   }
 
   int max_f = 1, max_x = 1;
 
  private:
   int find_run(const Chunk& c, bool& extend) const {
-    for (int k = 0; k < cur_.nx; ++k) {
-      const PXc& r = cur_.xc[k];
+    for (size_t k = 0; k < cur_.runs.size(); ++k) {
+      const Run& r = cur_.runs[k];
       if (r.buf != c.x_buf) continue;
       if (c.x_tile >= r.x_tile && c.x_tile + c.ks <= r.x_tile + r.tiles) {
         extend = false;
-        return k;
+        return (int)k;
       }
       if (c.x_tile == r.x_tile + r.tiles) {
         extend = true;
-        return k;
+        return (int)k;
       }
     }
     return -1;
   }
 
-  bool fits(const Chunk& c) const {
-    if (cur_.nb >= PB_MAX) return false;
-    if (ftiles_ + c.nt * c.ks > F_CAP_TILES) return false;
+  bool fits(const Chunk& c, int mode) const {
+    if ((int)cur_.ch.size() >= PB_MAX) return false;
+    if (cur_.ftiles + c.nt * c.ks > f_cap_) return false;
+    std::vector<Chunk> t = cur_.ch;
+    t.push_back(c);
+    if (count_items(t, mode, NTW_MIN) > MAX_ITEMS) return false;
     if (c.ks == 0) return true;
     bool extend = false;
     const int k = find_run(c, extend);
-    if (k < 0 && cur_.nx >= PX_MAX) return false;
+    if (k < 0 && (int)cur_.runs.size() >= PX_MAX) return false;
     const int add = (k < 0 || extend) ? c.ks : 0;
-    return xtiles_ + add <= X_CAP_TILES;
+    return cur_.xtiles + add <= X_CAP_TILES;
   }
 
   void place(const Chunk& c) {
-    PBlk& b = cur_.blk[cur_.nb++];
-    b.f_tile = c.f_tile;
-    b.y_tile = c.y_tile;
-    b.nt = c.nt;
-    b.ks = c.ks;
-    b.y_buf = c.y_buf;
-    b.xc = -1;
-    b.x_t = 0;
+    int k = -1, xt = 0;
     if (c.ks > 0) {
       bool extend = false;
-      int k = find_run(c, extend);
+      k = find_run(c, extend);
       if (k < 0) {
-        k = cur_.nx++;
-        cur_.xc[k].x_tile = c.x_tile;
-        cur_.xc[k].tiles = c.ks;
-        cur_.xc[k].buf = c.x_buf;
-        xtiles_ += c.ks;
+        k = (int)cur_.runs.size();
+        cur_.runs.push_back(Run{c.x_tile, c.ks, c.x_buf});
+        cur_.xtiles += c.ks;
       } else if (extend) {
-        cur_.xc[k].tiles += c.ks;
-        xtiles_ += c.ks;
+        cur_.runs[(size_t)k].tiles += c.ks;
+        cur_.xtiles += c.ks;
       }
-      b.xc = (short)k;
-      b.x_t = (short)(c.x_tile - cur_.xc[k].x_tile);
+      xt = (int)(c.x_tile - cur_.runs[(size_t)k].x_tile);
     }
-    ftiles_ += c.nt * c.ks;
+    cur_.ch.push_back(c);
+    cur_.ch_run.push_back(k);
+    cur_.ch_xt.push_back(xt);
+    cur_.ftiles += c.nt * c.ks;
   }
 
   void emit() {
-    max_f = std::max(max_f, ftiles_);
-    max_x = std::max(max_x, xtiles_);
-    out_.push_back(cur_);
-    reset();
+    max_f = std::max(max_f, cur_.ftiles);
+    max_x = std::max(max_x, cur_.xtiles);
+    out_.push_back(std::move(cur_));
+    cur_ = HostPiece();
   }
 
-  void reset() {
-    std::memset(&cur_, 0, sizeof(cur_));
-    ftiles_ = 0;
-    xtiles_ = 0;
-  }
-
-  std::vector<PRec>& out_;
-  PRec cur_;
-  int ftiles_ = 0, xtiles_ = 0;
+  std::vector<HostPiece>& out_;
+  int f_cap_;
+  HostPiece cur_;
 };
 
-// Cut one task into chunks of at most kc k-steps (kc nt tiles fit a piece).
-// A task that is one chunk is an independent product.
-static void task_chunks(const NatTask& L, std::vector<Chunk>& cs) {
+// The record of a piece for MT m-tiles: stage layout, copies, and the items
+// of every consumer warp (mode 0: largest item first to the least-loaded
+// warp; mode 1: warp g owns n-tile group g across all pieces of the task).
+static void encode(const HostPiece& p, int MT, PRec& r) {
+  std::memset(&r, 0, sizeof r);
+  const int ntw = HB_FLOW_TILES_PER_WARP / MT;
+  std::vector<int> f_soff(p.ch.size()), run_off(p.runs.size());
+  int off = 0, nc = 0;
+  for (size_t b = 0; b < p.ch.size(); ++b) {
+    f_soff[b] = off;
+    const int tiles = p.ch[b].nt * p.ch[b].ks;
+    if (tiles) r.cp[nc++] = PCopy{p.ch[b].f_tile, off, tiles | (3 << 28)};
+    off += tiles * 512;
+  }
+  r.f_bytes = off;
+  int xo = 0;
+  for (size_t k = 0; k < p.runs.size(); ++k) {
+    run_off[k] = xo;
+    r.cp[nc++] = PCopy{p.runs[k].x_tile, xo, p.runs[k].tiles | (p.runs[k].buf << 28)};
+    xo += p.runs[k].tiles;
+  }
+  r.x_tiles = xo;
+  r.ncopy = nc;
+  auto mk = [&](size_t b, int t0, int ntl, int flags) {
+    const Chunk& c = p.ch[b];
+    PItem it{};
+    it.y_tile = c.y_tile + t0;
+    it.f_soff = f_soff[b] + t0 * 512;
+    it.x_t = p.ch_run[b] >= 0 ? run_off[(size_t)p.ch_run[b]] + p.ch_xt[b] : 0;
+    it.ks = (short)c.ks;
+    it.f_stride = (short)c.nt;
+    it.ntl = (unsigned char)ntl;
+    it.y_buf = (unsigned char)c.y_buf;
+    it.flags = (unsigned char)flags;
+    return it;
+  };
+  std::vector<std::vector<PItem>> per((size_t)NCW);
+  if (p.mode == 0) {
+    const int ipt = mode0_ipt(p.ch, ntw);
+    std::vector<std::pair<long long, PItem>> items;
+    for (size_t b = 0; b < p.ch.size(); ++b)
+      for (int t0 = 0; t0 < p.ch[b].nt; t0 += ipt) {
+        const int ntl = std::min(ipt, p.ch[b].nt - t0);
+        items.push_back({(long long)ntl * std::max(1, p.ch[b].ks), mk(b, t0, ntl, 3)});
+      }
+    std::stable_sort(items.begin(), items.end(),
+                     [](const std::pair<long long, PItem>& a, const std::pair<long long, PItem>& b) {
+                       return a.first > b.first;
+                     });
+    std::vector<long long> load((size_t)NCW, 0);
+    for (const auto& w : items) {
+      const size_t m = (size_t)(std::min_element(load.begin(), load.end()) - load.begin());
+      per[m].push_back(w.second);
+      load[m] += w.first;
+    }
+  } else {
+    const int nt = p.ch[0].nt, ipt = mode1_ipt(nt);
+    for (int g = 0; g * ipt < nt; ++g)
+      for (size_t b = 0; b < p.ch.size(); ++b) {
+        int flags = 0;
+        if ((p.first_last & 1) && b == 0) flags |= 1;
+        if ((p.first_last & 2) && b + 1 == p.ch.size()) flags |= 2;
+        per[(size_t)g].push_back(mk(b, g * ipt, std::min(ipt, nt - g * ipt), flags));
+      }
+  }
+  int e = 0;
+  for (int w = 0; w < NCW; ++w) {
+    r.wbeg[w] = (unsigned char)e;
+    for (const PItem& it : per[(size_t)w]) {
+      if (e >= MAX_ITEMS) throw Error{HB_ERR_UNSUPPORTED, "piece record overflow"};
+      r.it[e++] = it;
+    }
+  }
+  r.wbeg[NCW] = (unsigned char)e;
+}
+
+// Cut one task into chunks of at most kc k-steps (kc nt tiles fit a piece
+// of f_cap tiles).  A task that is one chunk is an independent product.
+static void task_chunks(const NatTask& L, int f_cap, std::vector<Chunk>& cs) {
   if (L.nt > MAX_NT) throw Error{HB_ERR_UNSUPPORTED, "a factor block has more than 256 rows"};
-  const int kc = std::max(1, std::min(X_CAP_TILES, F_CAP_TILES / L.nt));
+  const int kc = std::max(1, std::min(X_CAP_TILES, f_cap / L.nt));
   cs.clear();
   for (const NatTerm& tm : L.terms)
     for (int k0 = 0; k0 < tm.ks; k0 += kc) {
@@ -690,13 +789,26 @@ void flow_plan_build(const std::vector<NatTask>& lt, void** plan_out) {
     int maxd = -1;
     for (const NatTask& L : lt) maxd = std::max(maxd, L.depth);
     P->depth_pieces.assign((size_t)(maxd + 1), {});
+    std::vector<long long> dtiles((size_t)(maxd + 1), 0);
+    for (const NatTask& L : lt)
+      for (const NatTerm& tm : L.terms) dtiles[(size_t)L.depth] += (long long)L.nt * tm.ks;
+    int dev = 0, nsm = 1;
+    HB_CUDA(cudaGetDevice(&dev));
+    HB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     std::vector<Chunk> cs;
     for (int d = 0; d <= maxd; ++d) {
+      // optionally, small depths get smaller pieces: about PIECES_PER_SM per SM
+      const int f_cap =
+          PIECES_PER_SM <= 0
+              ? F_CAP_TILES
+              : (int)std::max<long long>(MAX_NT, std::min<long long>(F_CAP_TILES, dtiles[(size_t)d] /
+                                                                                     ((long long)PIECES_PER_SM * nsm) /
+                                                                                     8 * 8));
       std::vector<Chunk> indep;
       std::vector<std::vector<Chunk>> accum;
       for (const NatTask& L : lt) {
         if (L.depth != d || L.nt == 0) continue;
-        task_chunks(L, cs);
+        task_chunks(L, f_cap, cs);
         if (cs.size() == 1) indep.push_back(cs[0]);
         else accum.push_back(cs);
       }
@@ -705,7 +817,7 @@ void flow_plan_build(const std::vector<NatTask>& lt, void** plan_out) {
         if (a.x_buf != b.x_buf) return a.x_buf < b.x_buf;
         return a.x_tile < b.x_tile;
       });
-      PieceBuilder pb(P->depth_pieces[(size_t)d]);
+      PieceBuilder pb(P->depth_pieces[(size_t)d], f_cap);
       for (const Chunk& c : indep) pb.add_independent(c);
       pb.flush();
       for (const auto& ch : accum) pb.add_task(ch);
@@ -719,27 +831,30 @@ void flow_plan_build(const std::vector<NatTask>& lt, void** plan_out) {
   *plan_out = P;
 }
 
-void flow_plan_free(void* plan) {
-  FlowPlan* P = static_cast<FlowPlan*>(plan);
-  if (!P) return;
-  for (DepthStreams& d : P->streams) {
+static void free_streams(std::vector<DepthStreams>& ss) {
+  for (DepthStreams& d : ss) {
     dev_free(d.d_recs);
     dev_free(d.d_off);
   }
+  ss.clear();
+}
+
+void flow_plan_free(void* plan) {
+  FlowPlan* P = static_cast<FlowPlan*>(plan);
+  if (!P) return;
+  for (auto& ss : P->streams) free_streams(ss);
   delete P;
 }
 
 int flow_plan_depths(const void* plan) { return (int)static_cast<const FlowPlan*>(plan)->depth_pieces.size(); }
 
-// Per-CTA piece streams of every depth for a maximum grid of gmax CTAs; the
-// pieces of one accumulating task stay together, in order, on one CTA.
-static void build_streams(FlowPlan* P, int gmax) {
-  for (DepthStreams& d : P->streams) {
-    dev_free(d.d_recs);
-    dev_free(d.d_off);
-  }
-  P->streams.clear();
-  for (const std::vector<PRec>& pcs : P->depth_pieces) {
+// Per-CTA record streams of every depth for a maximum grid of gmax CTAs and
+// MT m-tiles; the pieces of one accumulating task stay together, in order,
+// on one CTA.
+static void build_streams(FlowPlan* P, int gmax, int MT) {
+  std::vector<DepthStreams>& out = P->streams[MT];
+  free_streams(out);
+  for (const std::vector<HostPiece>& pcs : P->depth_pieces) {
     std::vector<std::vector<size_t>> units;
     for (size_t q = 0; q < pcs.size(); ++q) {
       if (pcs[q].mode == 1 && !(pcs[q].first_last & 1) && !units.empty()) units.back().push_back(q);
@@ -752,17 +867,20 @@ static void build_streams(FlowPlan* P, int gmax) {
     for (int b = 0; b < ds.grid; ++b) {
       off.push_back((long long)recs.size());
       for (size_t u = (size_t)b; u < units.size(); u += (size_t)ds.grid)
-        for (size_t q : units[u]) recs.push_back(pcs[q]);
+        for (size_t q : units[u]) {
+          recs.emplace_back();
+          encode(pcs[q], MT, recs.back());
+        }
     }
     off.push_back((long long)recs.size());
     if (ds.grid > 0) {
       ds.d_recs = upload(recs);
       ds.d_off = upload(off);
     }
-    P->streams.push_back(ds);
+    out.push_back(ds);
   }
   HB_CUDA(cudaDeviceSynchronize());
-  P->gmax = gmax;
+  P->gmax[MT] = gmax;
 }
 
 template <int MT>
@@ -784,10 +902,10 @@ static void launch_depths(FlowPlan* P, const uint4* F, uint4* x, uint4* y, uint4
   int per_sm = 0;
   HB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, (NCW + 1) * 32, smem));
   if (per_sm < 1) throw Error{HB_ERR_UNSUPPORTED, "step kernel does not fit on an SM"};
-  if (P->gmax != nsm * per_sm) build_streams(P, nsm * per_sm);
-  const int nd = (int)P->streams.size();
-  for (int d = 0; d < nd; ++d) {
-    const DepthStreams& ds = P->streams[(size_t)d];
+  if (P->gmax[MT] != nsm * per_sm) build_streams(P, nsm * per_sm, MT);
+  const std::vector<DepthStreams>& ss = P->streams[MT];
+  for (int d = 0; d < (int)ss.size(); ++d) {
+    const DepthStreams& ds = ss[(size_t)d];
     if (ds.grid == 0) continue;
     StepArgs args{ds.d_recs, ds.d_off, F, x, y, xh, stages, stage, budget, err};
     cudaLaunchConfig_t cfg = {};
