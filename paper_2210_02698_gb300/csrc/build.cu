@@ -471,6 +471,9 @@ void build(hb_ctx* c) {
     for (int dir = 0; dir < 2; ++dir) {
       std::vector<NatBlock> nb;
       long long ntile = 0;
+      // n-tiles per group: 4, and 2 for the many-term leaf outputs, whose
+      // accumulation chains are long (smaller groups balance them better)
+      int ng = 4;
       // a native block of op(F) with outputs (r1 | r2) and inputs (k1 | k2)
       auto nat = [&](long long src, int ld, int r1, int r2, int k1, int k2) {
         NatBlock B{};
@@ -482,6 +485,7 @@ void build(hb_ctx* c) {
         B.r2 = r2;
         B.k1 = k1;
         B.k2 = k2;
+        B.ng = ng;
         ntile += (tiles8(r1) + tiles8(r2)) * (tiles8(k1) + tiles8(k2));
         nb.push_back(B);
         return B.tile0;
@@ -501,6 +505,7 @@ void build(hb_ctx* c) {
         t.nt = (int)ntl;
         t.depth = depth;
         t.y_buf = y_buf;
+        t.ng = ng;
         return t;
       };
       if (dir == 0) {
@@ -530,6 +535,7 @@ void build(hb_ctx* c) {
               }
           }
         // last depth: y(leaf t) = D_t x(t) + sum over levels of K^L x_hat
+        ng = 2;
         for (long long t = 0; t < nleaf; ++t) {
           const int sz = leaf_size(t);
           NatTask o = task(c->leaf_tile[(size_t)t], tiles8(sz), Lmax + 1, 1);
@@ -579,6 +585,7 @@ void build(hb_ctx* c) {
               }
           }
         // last depth: y(leaf t) = D_t^H x(t) + sum over levels of V^0^H x_hat
+        ng = 2;
         for (long long t = 0; t < nleaf; ++t) {
           const int sz = leaf_size(t);
           NatTask o = task(c->leaf_tile[(size_t)t], tiles8(sz), Lmax + 1, 1);

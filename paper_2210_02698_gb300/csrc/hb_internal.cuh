@@ -97,16 +97,20 @@ struct Task {
 
 // Native (MMA-fragment) layout of the mixed apply (bf_mma.cu).  A factor
 // block op(F) (outputs x inputs) is stored as tiles of 8 outputs x 8 inputs
-// (512 bytes), ordered [k-step][n-tile]; rows of a block part are padded to
-// a multiple of 8 with zeros.  NatBlock says where a native block comes
-// from: the column-major FP64 block at src_off (leading dimension ld), op =
-// identity or conjugate transpose, outputs in one or two parts (r1, r2) and
-// inputs in one or two parts (k1, k2), each part padded on its own.
+// (512 bytes); the n-tiles are cut into groups of ng (the last group may be
+// smaller) and tiles are ordered [group][k-step][n-tile in group]; rows of a
+// block part are padded to a multiple of 8 with zeros.  NatBlock says where
+// a native block comes from: the column-major FP64 block at src_off
+// (leading dimension ld), op = identity or conjugate transpose, outputs in
+// one or two parts (r1, r2) and inputs in one or two parts (k1, k2), each
+// part padded on its own.
 struct NatBlock {
   long long src_off;
   long long tile0;       // first tile in the native arena
   int ld, conj;
   int r1, r2, k1, k2;
+  int ng;                // n-tiles per group
+  int pad;
 };
 // One term of a native task: ks k-steps of the block at f_tile, input row
 // tiles x_tile .. x_tile + ks of buffer x_buf (0 = x, 1 = y, 2 = xh).
@@ -123,6 +127,7 @@ struct NatTask {
   int nt;
   int depth;
   int y_buf;
+  int ng;                // n-tiles per group of its blocks
   std::vector<NatTerm> terms;
 };
 
