@@ -172,7 +172,6 @@ void ensure_scratch(hb_ctx* c, int nrhs) {
   if (!c->d_mx) {
     // native vectors for two m-tiles: 2 KB per row tile
     c->d_mx = dev_alloc<uint4>((size_t)std::max<long long>(c->nv_tiles, 1) * 128);
-    c->d_my = dev_alloc<uint4>((size_t)std::max<long long>(c->nv_tiles, 1) * 128);
     c->d_mxh = dev_alloc<uint4>((size_t)std::max<long long>(c->xh_tiles, 1) * 128);
   }
   if (!c->h_err) {
@@ -228,15 +227,12 @@ void apply_bf(hb_ctx* c, const double2* s, double2* u, int nrhs, int adjoint, in
       ts.begin("gather");
       gather_native(sc, c->d_pperm, c->d_mx, c->nv_tiles, c->Nv, R, MT, scale, st);
       ts.end();
-      // one launch per dependency depth; the timer brackets each launch
-      flow_launch(c->flow_plan[adjoint], c->d_nat[adjoint], c->d_mx, c->d_my, c->d_mxh, MT, c->d_err,
+      // one launch per dependency depth (the last one writes u); the timer brackets each launch
+      flow_launch(c->flow_plan[adjoint], c->d_nat[adjoint], c->d_mx, c->d_mxh, uc, c->d_pperm, c->Nv, R, c->d_err,
                   c->opt.barrier_cycles > 0 ? c->opt.barrier_cycles : (1LL << 31), st, [&](int, bool begin) {
                     if (begin) ts.begin(adjoint ? "bf_tc_adjoint" : "bf_tc");
                     else ts.end();
                   });
-      ts.begin("scatter");
-      scatter_native(c->d_my, c->d_pperm, uc, c->nv_tiles, c->Nv, R, MT, st);
-      ts.end();
     }
   }
   ts.finish();

@@ -78,7 +78,10 @@ namespace hb {
 constexpr int NWARP = HB_FLOW_WARPS;               // warps (streams) per CTA
 constexpr int ITEM_BYTES = HB_FLOW_ITEM_BYTES;     // stage bytes of one item at 2 m-tiles
 constexpr int MAX_STAGES = HB_FLOW_MAX_STAGES;     // ring stages per warp
-constexpr int NTW = 4;                             // largest n-tile group
+#ifndef HB_FLOW_NTW
+#define HB_FLOW_NTW 8
+#endif
+constexpr int NTW = HB_FLOW_NTW;                   // largest n-tile group (accumulators: 8 NTW MT registers)
 constexpr uint32_t IM_SIGN = 0x80000000u;          // sign bit of the imaginary (upper) bf16
 
 // One item (32 bytes): ks k-steps of one n-tile group of one term.
@@ -162,8 +165,11 @@ struct StepArgs {
   const long long* off;       // items of stream s (= CTA * NWARP + warp): [off[s], off[s + 1])
   const uint4* F;
   uint4* x;
-  uint4* y;
   uint4* xh;
+  double2* u;                 // outputs of buffer 1 go straight to u[rhs * Nv + natural index]
+  const long long* pperm;     // padded tree row -> natural index (-1: padding)
+  long long Nv;
+  int R;
   int stages;                 // ring stages per warp
   int stage_bytes;
   long long budget;
@@ -214,7 +220,17 @@ __device__ __forceinline__ void item_mma(const uint4* Fs, const uint4* Xs, int k
     case 2: item_mma_n<MT, 2>(Fs, Xs, ks, lane, acc); break;
     case 3: item_mma_n<MT, 3>(Fs, Xs, ks, lane, acc); break;
     case 4: item_mma_n<MT, 4>(Fs, Xs, ks, lane, acc); break;
-    default: break;
+    default:
+      if constexpr (NTW > 4) {
+        switch (ntl) {
+          case 5: item_mma_n<MT, 5>(Fs, Xs, ks, lane, acc); break;
+          case 6: item_mma_n<MT, 6>(Fs, Xs, ks, lane, acc); break;
+          case 7: item_mma_n<MT, 7>(Fs, Xs, ks, lane, acc); break;
+          case 8: item_mma_n<MT, 8>(Fs, Xs, ks, lane, acc); break;
+          default: break;
+        }
+      }
+      break;
   }
 }
 
@@ -239,6 +255,32 @@ __device__ __forceinline__ void store_tiles(uint4* Y, int ntl, int lane, const f
   }
 }
 
+// Store ntl n-tiles of the accumulators in natural order: element e of
+// lane (g, t) in tile j is row 8 (y_tile + j) + 2t + (e & 1), right-hand
+// side 16 mt + g + 8 (e >> 1); padded rows and right-hand sides >= R are
+// dropped.
+template <int MT>
+__device__ __forceinline__ void store_natural(const StepArgs& a, long long y_tile, int ntl, int lane,
+                                              const float (&acc)[NTW][MT][8]) {
+  const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+  for (int j = 0; j < NTW; ++j) {
+    if (j >= ntl) break;
+    const long long row = 8 * (y_tile + j) + 2 * t;
+    const long long nat0 = a.pperm[row], nat1 = a.pperm[row + 1];
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt) {
+      const float* v = acc[j][mt];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const long long nat = (e & 1) ? nat1 : nat0;
+        const int rhs = 16 * mt + g + 8 * (e >> 1);
+        if (nat >= 0 && rhs < a.R) a.u[(size_t)rhs * a.Nv + nat] = make_double2((double)v[e], (double)v[e + 4]);
+      }
+    }
+  }
+}
+
 template <int MT>
 __device__ __forceinline__ void zero_acc(float (&acc)[NTW][MT][8]) {
 #pragma unroll
@@ -257,7 +299,7 @@ __global__ void __launch_bounds__(NWARP * 32, 1) bf_step_kernel(StepArgs a) {
   __shared__ __align__(16) WItem slot[NWARP][MAX_STAGES];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nst = a.stages;
-  auto buf = [&](int id) { return id == 0 ? a.x : (id == 1 ? a.y : a.xh); };
+  auto buf = [&](int id) { return id == 0 ? a.x : a.xh; };   // inputs come from x or xh
   const long long sid = (long long)blockIdx.x * NWARP + warp;
   const long long ib = a.off[sid], n = a.off[sid + 1] - ib;
   unsigned char* ring = smem + (size_t)warp * nst * a.stage_bytes;
@@ -348,7 +390,10 @@ __global__ void __launch_bounds__(NWARP * 32, 1) bf_step_kernel(StepArgs a) {
     const uint4* st = reinterpret_cast<const uint4*>(ring + (size_t)s * a.stage_bytes);
     if (flags & 1) zero_acc<MT>(acc);
     if (ks > 0) item_mma<MT>(st, st + ntl * ks * 32, ks, ntl, lane, acc);
-    if (flags & 2) store_tiles<MT>(buf(w.y_buf) + (size_t)w.y_tile * (MT * 64), ntl, lane, acc);
+    if (flags & 2) {
+      if (w.y_buf == 1) store_natural<MT>(a, w.y_tile, ntl, lane, acc);
+      else store_tiles<MT>(a.xh + (size_t)w.y_tile * (MT * 64), ntl, lane, acc);
+    }
     // every lane's reads of stage s are done before lane 0 refills it
     __syncwarp();
     if (i + nst < n) issue(s, i + nst, true);
@@ -435,58 +480,49 @@ __device__ __forceinline__ void word_coords(long long q, int MT, long long& rt, 
   rhs = 16 * mt + (ln >> 2) + 8 * (j & 1);
 }
 
-// x (native) = pair(scale * s[rhs * Nv + natural index of the padded row])
-__global__ void gather_native_kernel(const double2* __restrict__ s, const long long* __restrict__ pperm,
-                                     uint32_t* __restrict__ x, long long nv_tiles, long long Nv, int R, int MT,
-                                     double scale) {
-  const long long total = nv_tiles * MT * 128;
-  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total;
-       q += (long long)gridDim.x * blockDim.x) {
-    long long rt, row;
-    int mt, w, rhs;
-    word_coords(q, MT, rt, mt, w, row, rhs);
-    const long long nat = pperm[row];
-    double2 v = make_double2(0.0, 0.0);
-    if (nat >= 0 && rhs < R) v = s[(size_t)rhs * Nv + nat];
-    const uint2 p = to_pair((float)(v.x * scale), (float)(v.y * scale));
-    uint32_t* tile = x + (rt * MT + mt) * 256;
-    tile[w] = p.x;
-    tile[128 + w] = p.y;
+// x (native) = pair(scale * s[rhs * Nv + natural index of the padded row]).
+// One warp per (row tile, m-tile): lane l reads rows l & 7, right-hand sides
+// 16 mt + 4 (l >> 3) + c (c < 4) - for each c, eight lanes read one 128-byte
+// run of a column when a leaf row is contiguous in natural order - and the
+// pairs are transposed through shared memory into fragment order.
+__global__ void __launch_bounds__(256) gather_native_kernel(const double2* __restrict__ s,
+                                                            const long long* __restrict__ pperm,
+                                                            uint4* __restrict__ x, long long nv_tiles, long long Nv,
+                                                            int R, int MT, double scale) {
+  __shared__ __align__(16) uint32_t tile[8][256];
+  const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
+  const long long wid = (long long)blockIdx.x * 8 + wb;
+  if (wid >= nv_tiles * MT) return;
+  const long long rt = wid / MT;
+  const int mt = (int)(wid - rt * MT);
+  const int r = lane & 7, c0 = 4 * (lane >> 3);
+  const long long nat = pperm[8 * rt + r];
+  double2 v[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int rhs = 16 * mt + c0 + c;
+    v[c] = (nat >= 0 && rhs < R) ? s[(size_t)rhs * Nv + nat] : make_double2(0.0, 0.0);
   }
-}
-
-__global__ void scatter_native_kernel(const uint32_t* __restrict__ y, const long long* __restrict__ pperm,
-                                      double2* __restrict__ u, long long nv_tiles, long long Nv, int R, int MT) {
-  const long long total = nv_tiles * MT * 128;
-  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total;
-       q += (long long)gridDim.x * blockDim.x) {
-    long long rt, row;
-    int mt, w, rhs;
-    word_coords(q, MT, rt, mt, w, row, rhs);
-    const long long nat = pperm[row];
-    if (nat < 0 || rhs >= R) continue;
-    const uint32_t* tile = y + (rt * MT + mt) * 256;
-    const uint32_t hi = tile[w], lo = tile[128 + w];
-    const double re = (double)__uint_as_float(hi << 16) + (double)__uint_as_float(lo << 16);
-    const double im = (double)__uint_as_float(hi & 0xffff0000u) + (double)__uint_as_float(lo & 0xffff0000u);
-    u[(size_t)rhs * Nv + nat] = make_double2(re, im);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int q = c0 + c;                               // right-hand side within the m-tile
+    const int dl = (q & 7) * 4 + (r >> 1);              // destination lane (g, t) = (q & 7, r >> 1)
+    const int dj = (r & 1) * 2 + (q >> 3);              // destination word
+    const uint2 p = to_pair((float)(v[c].x * scale), (float)(v[c].y * scale));
+    tile[wb][dl * 4 + dj] = p.x;
+    tile[wb][128 + dl * 4 + dj] = p.y;
   }
+  __syncwarp();
+  uint4* out = x + (size_t)wid * 64;   // tile (rt, mt) = rt * MT + mt = wid
+  out[lane] = reinterpret_cast<const uint4*>(tile[wb])[lane];
+  out[32 + lane] = reinterpret_cast<const uint4*>(tile[wb])[32 + lane];
 }
 
 void gather_native(const double2* s, const long long* pperm, uint4* x, long long nv_tiles, long long Nv, int R,
                    int MT, double scale, cudaStream_t st) {
-  const long long total = nv_tiles * MT * 128;
-  const int grid = (int)std::max<long long>(1, std::min<long long>((total + 255) / 256, 152LL * 16));
-  gather_native_kernel<<<grid, 256, 0, st>>>(s, pperm, reinterpret_cast<uint32_t*>(x), nv_tiles, Nv, R, MT, scale);
-  HB_CHECK_LAUNCH();
-}
-
-void scatter_native(const uint4* y, const long long* pperm, double2* u, long long nv_tiles, long long Nv, int R,
-                    int MT, cudaStream_t st) {
-  const long long total = nv_tiles * MT * 128;
-  const int grid = (int)std::max<long long>(1, std::min<long long>((total + 255) / 256, 152LL * 16));
-  scatter_native_kernel<<<grid, 256, 0, st>>>(reinterpret_cast<const uint32_t*>(y), pperm, u, nv_tiles, Nv, R,
-                                              MT);
+  const long long warps = nv_tiles * MT;
+  if (warps == 0) return;
+  gather_native_kernel<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(s, pperm, x, nv_tiles, Nv, R, MT, scale);
   HB_CHECK_LAUNCH();
 }
 
@@ -626,8 +662,9 @@ static void build_streams(FlowPlan* P, int grid) {
 }
 
 template <int MT>
-static void launch_depths(FlowPlan* P, const uint4* F, uint4* x, uint4* y, uint4* xh, int* err, long long budget,
-                          cudaStream_t st, const std::function<void(int, bool)>& timer) {
+static void launch_depths(FlowPlan* P, const uint4* F, uint4* x, uint4* xh, double2* u, const long long* pperm,
+                          long long Nv, int R, int* err, long long budget, cudaStream_t st,
+                          const std::function<void(int, bool)>& timer) {
   auto k = bf_step_kernel<MT>;
   int dev = 0, nsm = 0, optin = 0;
   HB_CUDA(cudaGetDevice(&dev));
@@ -648,7 +685,7 @@ static void launch_depths(FlowPlan* P, const uint4* F, uint4* x, uint4* y, uint4
   for (int d = 0; d < (int)P->streams.size(); ++d) {
     const DepthStreams& ds = P->streams[(size_t)d];
     if (ds.grid == 0) continue;
-    StepArgs args{ds.d_items, ds.d_off, F, x, y, xh, stages, stage, budget, err};
+    StepArgs args{ds.d_items, ds.d_off, F, x, xh, u, pperm, Nv, R, stages, stage, budget, err};
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(ds.grid);
     cfg.blockDim = dim3(NWARP * 32);
@@ -665,12 +702,14 @@ static void launch_depths(FlowPlan* P, const uint4* F, uint4* x, uint4* y, uint4
   }
 }
 
-void flow_launch(void* plan, const uint4* F, uint4* x, uint4* y, uint4* xh, int MT, int* err,
-                 long long budget_cycles, cudaStream_t st, const std::function<void(int, bool)>& timer) {
+void flow_launch(void* plan, const uint4* F, uint4* x, uint4* xh, double2* u, const long long* pperm, long long Nv,
+                 int R, int* err, long long budget_cycles, cudaStream_t st,
+                 const std::function<void(int, bool)>& timer) {
   FlowPlan* P = static_cast<FlowPlan*>(plan);
   if (P->chains.empty()) return;
-  if (MT == 1) launch_depths<1>(P, F, x, y, xh, err, budget_cycles, st, timer);
-  else if (MT == 2) launch_depths<2>(P, F, x, y, xh, err, budget_cycles, st, timer);
+  const int MT = (R + 15) / 16;
+  if (MT == 1) launch_depths<1>(P, F, x, xh, u, pperm, Nv, R, err, budget_cycles, st, timer);
+  else if (MT == 2) launch_depths<2>(P, F, x, xh, u, pperm, Nv, R, err, budget_cycles, st, timer);
   else throw Error{HB_ERR_UNSUPPORTED, "the mixed apply takes 1 or 2 m-tiles of 16 right-hand sides per pass"};
 }
 

@@ -35,6 +35,15 @@
 
 namespace hb {
 
+#ifndef HB_LEAF_NG
+#define HB_LEAF_NG 8
+#endif
+#ifndef HB_NG
+#define HB_NG 4
+#endif
+constexpr int LEAF_NG = HB_LEAF_NG;   // n-tiles per group of the leaf-output tasks (mixed apply)
+constexpr int BLOCK_NG = HB_NG;       // n-tiles per group of the other tasks
+
 struct BlockRec {
   int rank = 0;
   int ncols = 0;
@@ -471,9 +480,9 @@ void build(hb_ctx* c) {
     for (int dir = 0; dir < 2; ++dir) {
       std::vector<NatBlock> nb;
       long long ntile = 0;
-      // n-tiles per group: 4, and 2 for the many-term leaf outputs, whose
-      // accumulation chains are long (smaller groups balance them better)
-      int ng = 4;
+      // n-tiles per group: 4, and LEAF_NG for the many-term leaf outputs,
+      // whose accumulation chains are long (smaller groups balance better)
+      int ng = BLOCK_NG;
       // a native block of op(F) with outputs (r1 | r2) and inputs (k1 | k2)
       auto nat = [&](long long src, int ld, int r1, int r2, int k1, int k2) {
         NatBlock B{};
@@ -535,7 +544,7 @@ void build(hb_ctx* c) {
               }
           }
         // last depth: y(leaf t) = D_t x(t) + sum over levels of K^L x_hat
-        ng = 2;
+        ng = LEAF_NG;
         for (long long t = 0; t < nleaf; ++t) {
           const int sz = leaf_size(t);
           NatTask o = task(c->leaf_tile[(size_t)t], tiles8(sz), Lmax + 1, 1);
@@ -585,7 +594,7 @@ void build(hb_ctx* c) {
               }
           }
         // last depth: y(leaf t) = D_t^H x(t) + sum over levels of V^0^H x_hat
-        ng = 2;
+        ng = LEAF_NG;
         for (long long t = 0; t < nleaf; ++t) {
           const int sz = leaf_size(t);
           NatTask o = task(c->leaf_tile[(size_t)t], tiles8(sz), Lmax + 1, 1);

@@ -200,7 +200,6 @@ struct hb_ctx {
   void* d_xh = nullptr;
   // mixed apply scratch (native layout, up to 32 right-hand sides)
   uint4* d_mx = nullptr;
-  uint4* d_my = nullptr;
   uint4* d_mxh = nullptr;
 
   // timing
@@ -230,14 +229,13 @@ void id_batch_noalloc(int count, const int* m, const int* n, const long long* a_
 void flow_plan_build(const std::vector<NatTask>& tasks, void** plan_out);
 void flow_plan_free(void* plan);
 int flow_plan_depths(const void* plan);
-// MT = m-tiles of 16 right-hand sides (1 or 2)
-void flow_launch(void* plan, const uint4* F, uint4* x, uint4* y, uint4* xh, int MT, int* err,
-                 long long budget_cycles, cudaStream_t st, const std::function<void(int, bool)>& timer);
+// R <= 32 right-hand sides; the last depth writes u (natural order) itself
+void flow_launch(void* plan, const uint4* F, uint4* x, uint4* xh, double2* u, const long long* pperm, long long Nv,
+                 int R, int* err, long long budget_cycles, cudaStream_t st,
+                 const std::function<void(int, bool)>& timer);
 void nat_convert(const double2* F64, const std::vector<NatBlock>& blocks, uint4* out, cudaStream_t st);
 void gather_native(const double2* s, const long long* pperm, uint4* x, long long nv_tiles, long long Nv, int R,
                    int MT, double scale, cudaStream_t st);
-void scatter_native(const uint4* y, const long long* pperm, double2* u, long long nv_tiles, long long Nv, int R,
-                    int MT, cudaStream_t st);
 void apply_bf(hb_ctx* c, const double2* s, double2* u, int nrhs, int adjoint, int precision,
               cudaStream_t st);
 void tree_build(hb_ctx* c);
