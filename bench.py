@@ -106,6 +106,40 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
+PROFILE = os.path.join(ROOT, "profiles", "bf_step_kernel_grad256.md")
+KERNEL_SOURCES = ["paper_2210_02698_gb300/csrc/bf_mma.cu", "paper_2210_02698_gb300/csrc/build.cu"]
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes (read + write) of the step kernels of one apply from the
+    committed ncu summary, if it was taken on the current kernel sources."""
+    try:
+        with open(PROFILE) as f:
+            txt = f.read()
+    except OSError:
+        return None
+    vals = {}
+    for line in txt.splitlines():
+        if line.startswith("- ") and ":" in line:
+            k, v = line[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel sources sha256[:16]") != kernel_source_hash():
+        return None
+    try:
+        return float(vals["step-kernel DRAM bytes per apply"])
+    except (KeyError, ValueError):
+        return None
+
+
 def cpu_oracle_sample(w, tables, rows_n, seed=1234):
     """Time the oracle's dense sum on a bounded sample of output rows."""
     import oracle.dense as odense
@@ -223,7 +257,6 @@ def run_ours(args):
         apply_mixed()
     ktimes = op.kernel_times()
     op.set_kernel_timing(False)
-    launches_per_apply = sum(int(c) for _, c in ktimes.values()) // nk
 
     # ---- plain FP64 GPU butterfly apply (same factors, complex128)
     op.set_precision(binding.HB_FP64)
@@ -254,16 +287,17 @@ def run_ours(args):
         E = info["factor_entries"]
         fac_bytes = E * 8
         # algorithmic bytes of the step kernels of one apply: every factor entry
-        # once (FP32 complex), the tree-ordered input read once, the output
-        # written once, every skeleton vector written once and read once
-        alg_bytes = fac_bytes + 2 * Nv * R * 8 + 2 * info["skeleton_rows"] * R * 8
+        # once (8-byte split-BF16 pair), the tree-ordered input read once
+        # (8-byte pairs), the output written once (FP64 complex), every
+        # skeleton vector written once and read once (8-byte pairs)
+        alg_bytes = fac_bytes + Nv * R * (8 + 16) + 2 * info["skeleton_rows"] * R * 8
         achieved = alg_bytes / (step_ms * 1e-3) / 1e9
         value = Nv * R * world / (ms * 1e-3)
         nc = cores()
         # cpu baseline: oracle dense sum on a bounded row sample, plus the
         # rel-L2 of our mixed output on those rows
         cpu = {}
-        rows_n = 8
+        rows_n = 384   # about 15 s of the oracle on the host cores
         try:
             if args.skip_cpu:
                 raise RuntimeError("skipped (--skip-cpu)")
@@ -280,19 +314,21 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
             "config": {"workload": "grad256: c=1+0.5z, 256x256 cells (N_v=65536), omega=2pi*32, n_I=16, "
                                    "eps=1e-6, chi=20, leaf 64, 16 complex Gaussian RHS",
                        "l2": f"factors {fac_bytes / 2**20:.0f} MiB > 129 MB L2, no flush",
-                       "precision": "FP32 factors/vectors, split-BF16x3 products, FP32 accumulate",
+                       "precision": "factors and vectors as split-BF16 pairs (hi + lo), three BF16 "
+                                    "tensor-core products per complex MAC, FP32 accumulate, FP64 output",
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": None,
-                         "kernel": "butterfly step kernels of one apply",
+                         "frac": achieved / hbm, "traffic": profiled_traffic(),
+                         "kernel": "butterfly step kernels of one apply (one launch per dependency depth)",
+                         "alg_bytes": alg_bytes, "kernel_ms": step_ms,
                          "peak_kind": f"{peak_kind} copy bandwidth"},
             "e2e": {"value": Nv * R * world / (ms_e2e * 1e-3), "unit": UNIT,
                     "h2d_bytes_per_step": Nv * R * 16, "d2h_bytes_per_step": Nv * R * 16},
-            "gpu_launches": launches_per_apply * args.steps,
+            "gpu_launches": info["apply_launches"] * args.steps,
             "clocks": clk,
             "cpu_baseline": cpu,
             "fp64_gpu": {"value": Nv * R * world / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64},

@@ -105,7 +105,8 @@ typedef struct {
   long long sampled_entries;  /* matrix entries evaluated by the build      */
   double build_ms;
   int built;
-  int apply_launches;         /* kernels launched by one hb_apply           */
+  int apply_launches;         /* kernels launched by one mixed-precision
+                                 hb_apply of up to 32 right-hand sides     */
   long long skeleton_rows;    /* sum of all ranks: rows of skeleton vectors */
 } hb_stats;
 

@@ -682,6 +682,7 @@ static void launch_depths(FlowPlan* P, const uint4* F, uint4* x, uint4* xh, doub
   HB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NWARP * 32, smem));
   if (per_sm < 1) throw Error{HB_ERR_UNSUPPORTED, "step kernel does not fit on an SM"};
   if (P->grid != nsm * per_sm) build_streams(P, nsm * per_sm);
+  bool first = true;   // the timer brackets all depth launches (PDL stays intact)
   for (int d = 0; d < (int)P->streams.size(); ++d) {
     const DepthStreams& ds = P->streams[(size_t)d];
     if (ds.grid == 0) continue;
@@ -696,10 +697,11 @@ static void launch_depths(FlowPlan* P, const uint4* F, uint4* x, uint4* xh, doub
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    timer(d, true);
+    if (first) timer(0, true);
+    first = false;
     HB_CUDA(cudaLaunchKernelEx(&cfg, k, args));
-    timer(d, false);
   }
+  if (!first) timer(0, false);
 }
 
 void flow_launch(void* plan, const uint4* F, uint4* x, uint4* xh, double2* u, const long long* pperm, long long Nv,

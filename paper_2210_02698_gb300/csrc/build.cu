@@ -626,10 +626,9 @@ void build(hb_ctx* c) {
   c->stats.id_blocks = id_blocks;
   c->stats.sampled_entries = sampled;
   c->stats.skeleton_rows = c->xh_rows;
-  int launches = 2;
-  for (size_t s = 0; s + 1 < c->step_begin[0].size(); ++s)
-    if (c->step_begin[0][s + 1] > c->step_begin[0][s]) ++launches;
-  c->stats.apply_launches = launches;
+  // mixed-precision apply of up to 32 right-hand sides: the gather and one
+  // step launch per dependency depth (the last one writes u)
+  c->stats.apply_launches = 1 + flow_plan_depths(c->flow_plan[0]);
   c->stats.build_ms =
       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_begin).count();
 }
