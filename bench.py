@@ -132,7 +132,7 @@ def profiled_traffic():
         if line.startswith("- ") and ":" in line:
             k, v = line[2:].split(":", 1)
             vals[k.strip()] = v.strip().strip("`")
-    if vals.get("kernel sources sha256[:16]") != kernel_source_hash():
+    if vals.get("kernel sources sha256 prefix") != kernel_source_hash():
         return None
     try:
         return float(vals["step-kernel DRAM bytes per apply"])
