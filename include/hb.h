@@ -80,8 +80,13 @@ typedef struct {
  * uniform proxy rows and nbr_radius_h: neighbour radius in units of h
  * (Eq. proxyv2v); precision: HB_FP64 or HB_MIXED_BF16X3 for hb_apply /
  * hb_apply_adjoint; workspace_mb: device workspace bound for the build
- * (0 = default); barrier_cycles: spin budget of bounded device waits
- * (0 = default). */
+ * (0 = default); barrier_cycles: spin budget (SM clock cycles, counted from
+ * the start of each kernel) of the bounded device waits of the mixed apply
+ * (0 = default, 2^31).  A wait that runs out sets a mapped error word; the
+ * kernel then lets its copies in flight land (waiting at least 2^31 cycles
+ * for them) and stops, and the next hb_apply / hb_apply_adjoint on the
+ * handle returns HB_ERR_TIMEOUT (the outputs of the apply that ran out are
+ * undefined). */
 typedef struct {
   double eps;
   int leaf;
@@ -141,6 +146,17 @@ hb_status hb_apply_adjoint(hb_handle h, const void* u, void* s, int nrhs, void* 
 
 /* hb_set_precision: HB_FP64 or HB_MIXED_BF16X3 for later applies. */
 hb_status hb_set_precision(hb_handle h, int precision);
+
+/* hb_set_wait_selftest: failure-detection self-test of the mixed apply (no
+ * counterpart in the paper).  When on != 0, the first warp of every step
+ * launch of later mixed applies also waits - with the same bounded wait as
+ * the data waits and the handle's barrier_cycles budget - on an mbarrier
+ * that nothing completes; the wait runs out and sets the mapped error word,
+ * and the apply otherwise completes normally, so the next hb_apply /
+ * hb_apply_adjoint returns HB_ERR_TIMEOUT.  No fault or hang is involved;
+ * each launch spends about barrier_cycles SM cycles in the wait.
+ * Errors: HB_ERR_ARG for a null handle. */
+hb_status hb_set_wait_selftest(hb_handle h, int on);
 
 /* hb_apply_dense / hb_apply_dense_adjoint: the same sums (Eq. m_v2v) and
  * their adjoint, matrix free, every entry evaluated in FP64 on the fly

@@ -21,7 +21,7 @@ STATUS = {0: "HB_OK", 1: "HB_ERR_ARG", 2: "HB_ERR_CUDA", 3: "HB_ERR_OOM", 4: "HB
           5: "HB_ERR_STATE", 6: "HB_ERR_UNSUPPORTED"}
 
 # every symbol include/hb.h declares
-EXPORTS = ["hb_create", "hb_build", "hb_apply", "hb_apply_adjoint", "hb_set_precision",
+EXPORTS = ["hb_create", "hb_build", "hb_apply", "hb_apply_adjoint", "hb_set_precision", "hb_set_wait_selftest",
            "hb_apply_dense", "hb_apply_dense_adjoint", "hb_entries", "hb_id_batch", "hb_id_batch_noalloc",
            "hb_tree_perm", "hb_proxy_rows", "hb_info", "hb_set_kernel_timing",
            "hb_kernel_times", "hb_last_error", "hb_destroy"]
@@ -68,6 +68,7 @@ def lib():
         for f in ("hb_apply", "hb_apply_adjoint", "hb_apply_dense", "hb_apply_dense_adjoint"):
             getattr(L, f).argtypes = [vp, vp, vp, i, vp]
         L.hb_set_precision.argtypes = [vp, i]
+        L.hb_set_wait_selftest.argtypes = [vp, i]
         L.hb_entries.argtypes = [vp, vp, i, vp, i, vp, vp]
         L.hb_id_batch.argtypes = [i, vp, vp, vp, vp, d, vp, vp, vp]
         L.hb_id_batch_noalloc.argtypes = [i, vp, vp, vp, vp, d, vp, vp, vp, vp]
@@ -116,7 +117,7 @@ class Operator:
 
     def __init__(self, N, nodes, tau2, v0, v1, n_cells, omega, eps=1e-6, leaf=64, chi=20.0,
                  nbr_radius_h=10.0, precision=HB_MIXED_BF16X3, workspace_mb=0, h=None,
-                 x0=0.0, y0=0.0):
+                 x0=0.0, y0=0.0, barrier_cycles=0):
         L = lib()
         self._keep = [np.ascontiguousarray(a, dtype=np.float64) for a in (nodes, tau2, v0, v1, n_cells)]
         nodes, tau2, v0, v1, n_cells = self._keep
@@ -127,7 +128,7 @@ class Operator:
         g = Grid(nx, ny, x0, y0, self.h)
         t = Tables(len(nodes), nodes.ctypes.data, nodes.ctypes.data, tau2.ctypes.data,
                    v0.ctypes.data, v1.ctypes.data, n_cells.ctypes.data)
-        o = Options(eps, leaf, chi, nbr_radius_h, precision, workspace_mb, 0)
+        o = Options(eps, leaf, chi, nbr_radius_h, precision, workspace_mb, int(barrier_cycles))
         hnd = C.c_void_p()
         _check(L.hb_create(C.byref(g), C.byref(t), float(omega), C.byref(o), C.byref(hnd)))
         self.handle = hnd
@@ -151,6 +152,10 @@ class Operator:
 
     def set_precision(self, p):
         self._call("hb_set_precision", int(p))
+
+    def set_wait_selftest(self, on):
+        """Failure-detection self-test of the bounded device waits (see hb.h)."""
+        self._call("hb_set_wait_selftest", 1 if on else 0)
 
     def apply(self, s, u, nrhs, stream=None):
         self._call("hb_apply", _ptr(s), _ptr(u), int(nrhs), _stream_ptr(stream))

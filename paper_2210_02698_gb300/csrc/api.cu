@@ -148,6 +148,13 @@ hb_status hb_set_precision(hb_handle h, int precision) {
   });
 }
 
+hb_status hb_set_wait_selftest(hb_handle h, int on) {
+  return guarded(h, [&] {
+    if (!h) throw hb::arg_error("null handle");
+    h->wait_selftest = on != 0;
+  });
+}
+
 hb_status hb_apply_dense(hb_handle h, const void* s, void* u, int nrhs, void* stream) {
   return guarded(h, [&] {
     check_vec_args(h, s, u, nrhs);

@@ -229,7 +229,8 @@ void apply_bf(hb_ctx* c, const double2* s, double2* u, int nrhs, int adjoint, in
       ts.end();
       // one launch per dependency depth (the last one writes u); the timer brackets all of them
       flow_launch(c->flow_plan[adjoint], c->d_nat[adjoint], c->d_mx, c->d_mxh, uc, c->d_pperm, c->Nv, R, c->d_err,
-                  c->opt.barrier_cycles > 0 ? c->opt.barrier_cycles : (1LL << 31), st, [&](int, bool begin) {
+                  c->opt.barrier_cycles > 0 ? c->opt.barrier_cycles : (1LL << 31), c->wait_selftest, st,
+                  [&](int, bool begin) {
                     if (begin) ts.begin(adjoint ? "bf_tc_adjoint" : "bf_tc");
                     else ts.end();
                   });

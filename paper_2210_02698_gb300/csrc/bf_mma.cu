@@ -174,6 +174,7 @@ struct StepArgs {
   int stage_bytes;
   long long budget;
   int* err;
+  int selftest;               // the first warp also waits on a barrier nothing completes
 };
 
 // Accumulate ks k-steps of an item into acc: NTL n-tiles whose tiles are
@@ -306,12 +307,19 @@ __global__ void __launch_bounds__(NWARP * 32, 1) bf_step_kernel(StepArgs a) {
   uint64_t* bar = full[warp];
   WItem* sl = slot[warp];
 
+  __shared__ uint64_t never;   // failure-detection self-test: nothing arrives on it
   if (lane == 0) {
     for (int s = 0; s < nst; ++s) mbar_init(&bar[s], 1);
+    if (warp == 0) mbar_init(&never, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncwarp();
   const long long deadline = clock64() + a.budget;
+  if (a.selftest && blockIdx.x == 0 && warp == 0) {
+    const bool ok = mbar_wait_until(&never, 0u, deadline);
+    if (lane == 0 && !ok) *reinterpret_cast<volatile int*>(a.err) = 1;
+    __syncwarp();
+  }
 
   // Item records: the warp keeps two windows of 32 in registers (lane j
   // holds record 32 w + j of window w), loading window w + 1 when the first
@@ -404,8 +412,9 @@ __global__ void __launch_bounds__(NWARP * 32, 1) bf_step_kernel(StepArgs a) {
     if (lane == 0) {
       *reinterpret_cast<volatile int*>(a.err) = 1;
       const long long last = (i + nst < n) ? i + nst : n;
+      const long long drain = a.budget > (1LL << 31) ? a.budget : (1LL << 31);
       for (long long j = i; j < last; ++j)
-        mbar_wait_until(&bar[j % nst], (uint32_t)((j / nst) & 1), clock64() + a.budget);
+        mbar_wait_until(&bar[j % nst], (uint32_t)((j / nst) & 1), clock64() + drain);
     }
     __syncwarp();
   }
@@ -663,7 +672,7 @@ static void build_streams(FlowPlan* P, int grid) {
 
 template <int MT>
 static void launch_depths(FlowPlan* P, const uint4* F, uint4* x, uint4* xh, double2* u, const long long* pperm,
-                          long long Nv, int R, int* err, long long budget, cudaStream_t st,
+                          long long Nv, int R, int* err, long long budget, bool selftest, cudaStream_t st,
                           const std::function<void(int, bool)>& timer) {
   auto k = bf_step_kernel<MT>;
   int dev = 0, nsm = 0, optin = 0;
@@ -686,7 +695,7 @@ static void launch_depths(FlowPlan* P, const uint4* F, uint4* x, uint4* xh, doub
   for (int d = 0; d < (int)P->streams.size(); ++d) {
     const DepthStreams& ds = P->streams[(size_t)d];
     if (ds.grid == 0) continue;
-    StepArgs args{ds.d_items, ds.d_off, F, x, xh, u, pperm, Nv, R, stages, stage, budget, err};
+    StepArgs args{ds.d_items, ds.d_off, F, x, xh, u, pperm, Nv, R, stages, stage, budget, err, selftest ? 1 : 0};
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(ds.grid);
     cfg.blockDim = dim3(NWARP * 32);
@@ -705,13 +714,13 @@ static void launch_depths(FlowPlan* P, const uint4* F, uint4* x, uint4* xh, doub
 }
 
 void flow_launch(void* plan, const uint4* F, uint4* x, uint4* xh, double2* u, const long long* pperm, long long Nv,
-                 int R, int* err, long long budget_cycles, cudaStream_t st,
+                 int R, int* err, long long budget_cycles, bool selftest, cudaStream_t st,
                  const std::function<void(int, bool)>& timer) {
   FlowPlan* P = static_cast<FlowPlan*>(plan);
   if (P->chains.empty()) return;
   const int MT = (R + 15) / 16;
-  if (MT == 1) launch_depths<1>(P, F, x, xh, u, pperm, Nv, R, err, budget_cycles, st, timer);
-  else if (MT == 2) launch_depths<2>(P, F, x, xh, u, pperm, Nv, R, err, budget_cycles, st, timer);
+  if (MT == 1) launch_depths<1>(P, F, x, xh, u, pperm, Nv, R, err, budget_cycles, selftest, st, timer);
+  else if (MT == 2) launch_depths<2>(P, F, x, xh, u, pperm, Nv, R, err, budget_cycles, selftest, st, timer);
   else throw Error{HB_ERR_UNSUPPORTED, "the mixed apply takes 1 or 2 m-tiles of 16 right-hand sides per pass"};
 }
 

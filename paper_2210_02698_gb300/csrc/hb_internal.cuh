@@ -190,6 +190,7 @@ struct hb_ctx {
   void* flow_plan[2] = {nullptr, nullptr};  // mixed apply plans (bf_mma.cu)
   int* h_err = nullptr;                    // mapped pinned error word of bounded device waits
   int* d_err = nullptr;
+  bool wait_selftest = false;              // hb_set_wait_selftest
   long long xh_rows = 0;
   int max_rank = 0;
 
@@ -231,7 +232,7 @@ void flow_plan_free(void* plan);
 int flow_plan_depths(const void* plan);
 // R <= 32 right-hand sides; the last depth writes u (natural order) itself
 void flow_launch(void* plan, const uint4* F, uint4* x, uint4* xh, double2* u, const long long* pperm, long long Nv,
-                 int R, int* err, long long budget_cycles, cudaStream_t st,
+                 int R, int* err, long long budget_cycles, bool selftest, cudaStream_t st,
                  const std::function<void(int, bool)>& timer);
 void nat_convert(const double2* F64, const std::vector<NatBlock>& blocks, uint4* out, cudaStream_t st);
 void gather_native(const double2* s, const long long* pperm, uint4* x, long long nv_tiles, long long Nv, int R,
