@@ -144,6 +144,32 @@ hb_status hb_apply(hb_handle h, const void* s, void* u, int nrhs, void* stream);
  * blocks).  Same layout, limits and errors as hb_apply. */
 hb_status hb_apply_adjoint(hb_handle h, const void* u, void* s, int nrhs, void* stream);
 
+/* hb_save: write the built operator to a file: the creation inputs (grid,
+ * omega, options, tables, n_cells), the cluster tree, the FP64 factor arena
+ * and the factor index; hb_load reads it back into a new, built handle (the
+ * tree is rebuilt from the grid and must agree with the file).  The file is
+ * little-endian with every integer int64 and every real double:
+ *   "HBFACT01" | nx ny | x0 y0 h omega | eps chi nbr_radius_h |
+ *   leaf precision workspace_mb barrier_cycles | n_I | nodes_x[n_I]
+ *   nodes_y[n_I] | tau2, v0, v1 [N_I^2 each] | n_cells[N_v] | L_v |
+ *   perm[N_v] (tree position -> natural index) | bounds of tree levels
+ *   l = 0..L_v (2^l + 1 tree positions each) | n_factor |
+ *   arena[n_factor] (complex128, re then im) | leaf_off[2^L_v] |
+ *   n_butterfly | per butterfly (levels l = 1..L_v, sibling pairs p,
+ *   (oi, si) = (2p, 2p + 1) then (2p + 1, 2p)): l oi si L, then (rank,
+ *   f_off) of every block (i, j) of every level k = 0..L in the order
+ *   k, i 2^(L-k) + j, then kl_off[2^L].
+ * Blocks are column-major at their arena offset: dense leaf t |t| x |t|;
+ * V^0 block j rank x |leaf si 2^L + j|; W^k block (i, j) rank x (r1 + r2)
+ * with r1, r2 the ranks of level k-1 blocks (i/2) 2^(L-k+1) + 2j and + 1;
+ * K^L block i |leaf oi 2^L + i| x rank of level-L block i (Sec. 4.2.1,
+ * Eq. butterfly_mat; Sec. 4.2 HODBF; the paper has no file format).
+ * Synchronous.  Errors: HB_ERR_STATE (hb_save before hb_build), HB_ERR_ARG
+ * (unwritable path, unreadable, truncated or inconsistent file), HB_ERR_OOM,
+ * HB_ERR_CUDA. */
+hb_status hb_save(hb_handle h, const char* path);
+hb_status hb_load(const char* path, hb_handle* out);
+
 /* hb_set_precision: HB_FP64 or HB_MIXED_BF16X3 for later applies. */
 hb_status hb_set_precision(hb_handle h, int precision);
 

@@ -21,7 +21,8 @@ STATUS = {0: "HB_OK", 1: "HB_ERR_ARG", 2: "HB_ERR_CUDA", 3: "HB_ERR_OOM", 4: "HB
           5: "HB_ERR_STATE", 6: "HB_ERR_UNSUPPORTED"}
 
 # every symbol include/hb.h declares
-EXPORTS = ["hb_create", "hb_build", "hb_apply", "hb_apply_adjoint", "hb_set_precision", "hb_set_wait_selftest",
+EXPORTS = ["hb_create", "hb_build", "hb_save", "hb_load", "hb_apply", "hb_apply_adjoint", "hb_set_precision",
+           "hb_set_wait_selftest",
            "hb_apply_dense", "hb_apply_dense_adjoint", "hb_entries", "hb_id_batch", "hb_id_batch_noalloc",
            "hb_tree_perm", "hb_proxy_rows", "hb_info", "hb_set_kernel_timing",
            "hb_kernel_times", "hb_last_error", "hb_destroy"]
@@ -68,6 +69,8 @@ def lib():
         for f in ("hb_apply", "hb_apply_adjoint", "hb_apply_dense", "hb_apply_dense_adjoint"):
             getattr(L, f).argtypes = [vp, vp, vp, i, vp]
         L.hb_set_precision.argtypes = [vp, i]
+        L.hb_save.argtypes = [vp, C.c_char_p]
+        L.hb_load.argtypes = [C.c_char_p, vp]
         L.hb_set_wait_selftest.argtypes = [vp, i]
         L.hb_entries.argtypes = [vp, vp, i, vp, i, vp, vp]
         L.hb_id_batch.argtypes = [i, vp, vp, vp, vp, d, vp, vp, vp]
@@ -146,6 +149,26 @@ class Operator:
 
     def _call(self, name, *args):
         _check(getattr(lib(), name)(self.handle, *args), self.handle)
+
+    def save(self, path):
+        """Write the built operator to a file (hb_save)."""
+        self._call("hb_save", os.fsencode(str(path)))
+
+    @classmethod
+    def load(cls, path):
+        """A built operator read from a file written by save (hb_load)."""
+        L = lib()
+        hnd = C.c_void_p()
+        _check(L.hb_load(os.fsencode(str(path)), C.byref(hnd)))
+        self = cls.__new__(cls)
+        self.handle = hnd
+        self._keep = []
+        with open(path, "rb") as f:           # nx, ny and h from the file's header
+            head = f.read(48)
+        nx, ny = (int(v) for v in np.frombuffer(head, dtype="<i8", count=2, offset=8))
+        self.nx, self.ny, self.Nv = nx, ny, nx * ny
+        self.h = float(np.frombuffer(head, dtype="<f8", count=1, offset=40)[0])
+        return self
 
     def build(self):
         self._call("hb_build")

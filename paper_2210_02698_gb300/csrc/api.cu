@@ -57,30 +57,31 @@ void check_vec_args(hb_ctx* c, const void* a, const void* b, int nrhs) {
 
 extern "C" {
 
-hb_status hb_create(const hb_grid* grid, const hb_tables* tables, double omega, const hb_options* opts,
-                    hb_handle* out) {
-  hb_ctx* c = nullptr;
-  hb_status st = guarded(nullptr, [&] {
-    if (!grid || !tables || !opts || !out) throw hb::arg_error("null argument");
-    *out = nullptr;
-    if (grid->nx < 1 || grid->ny < 1 || !(grid->h > 0)) throw hb::arg_error("bad grid");
-    if ((long long)grid->nx * grid->ny > (1LL << 31)) throw hb::arg_error("grid too large");
-    if (tables->n_I < 2 || tables->n_I > 16)
-      throw hb::Error{tables->n_I < 2 ? HB_ERR_ARG : HB_ERR_UNSUPPORTED, "n_I must be in [2, 16]"};
-    if (!tables->nodes_x || !tables->nodes_y || !tables->tau2 || !tables->v0 || !tables->v1 ||
-        !tables->n_cells)
-      throw hb::arg_error("null table pointer");
-    if (!(omega > 0) || !std::isfinite(omega)) throw hb::arg_error("omega must be positive");
-    if (!(opts->eps > 0) || opts->leaf < 1 || !(opts->chi > 0) || !(opts->nbr_radius_h >= 0))
-      throw hb::arg_error("bad options (eps > 0, leaf >= 1, chi > 0, radius >= 0)");
-    if (opts->precision != HB_FP64 && opts->precision != HB_MIXED_BF16X3)
-      throw hb::arg_error("unknown precision %d", opts->precision);
-    int ndev = 0;
-    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
-      cudaGetLastError();
-      throw hb::Error{HB_ERR_CUDA, "no CUDA device"};
-    }
-    c = new hb_ctx();
+}  // extern "C"
+
+namespace hb {
+// Validate the inputs, copy them, upload the tables and build the cluster
+// tree; throws hb::Error.  Shared by hb_create and hb_load.
+hb_ctx* create_ctx(const hb_grid* grid, const hb_tables* tables, double omega, const hb_options* opts) {
+  if (!grid || !tables || !opts) throw hb::arg_error("null argument");
+  if (grid->nx < 1 || grid->ny < 1 || !(grid->h > 0)) throw hb::arg_error("bad grid");
+  if ((long long)grid->nx * grid->ny > (1LL << 31)) throw hb::arg_error("grid too large");
+  if (tables->n_I < 2 || tables->n_I > 16)
+    throw hb::Error{tables->n_I < 2 ? HB_ERR_ARG : HB_ERR_UNSUPPORTED, "n_I must be in [2, 16]"};
+  if (!tables->nodes_x || !tables->nodes_y || !tables->tau2 || !tables->v0 || !tables->v1 || !tables->n_cells)
+    throw hb::arg_error("null table pointer");
+  if (!(omega > 0) || !std::isfinite(omega)) throw hb::arg_error("omega must be positive");
+  if (!(opts->eps > 0) || opts->leaf < 1 || !(opts->chi > 0) || !(opts->nbr_radius_h >= 0))
+    throw hb::arg_error("bad options (eps > 0, leaf >= 1, chi > 0, radius >= 0)");
+  if (opts->precision != HB_FP64 && opts->precision != HB_MIXED_BF16X3)
+    throw hb::arg_error("unknown precision %d", opts->precision);
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    throw hb::Error{HB_ERR_CUDA, "no CUDA device"};
+  }
+  hb_ctx* c = new hb_ctx();
+  try {
     c->nx = grid->nx;
     c->ny = grid->ny;
     c->Nv = (long long)grid->nx * grid->ny;
@@ -102,15 +103,46 @@ hb_status hb_create(const hb_grid* grid, const hb_tables* tables, double omega, 
     hb::tree_build(c);
     c->stats.n_v = c->Nv;
     c->stats.levels = c->Lv;
-  });
-  if (st != HB_OK) {
-    if (c) {
-      g_err = c->err;
-      free_all(c);
-      delete c;
-    }
-    return st;
+  } catch (...) {
+    free_all(c);
+    delete c;
+    throw;
   }
+  return c;
+}
+}  // namespace hb
+
+extern "C" {
+
+hb_status hb_create(const hb_grid* grid, const hb_tables* tables, double omega, const hb_options* opts,
+                    hb_handle* out) {
+  hb_ctx* c = nullptr;
+  hb_status st = guarded(nullptr, [&] {
+    if (!out) throw hb::arg_error("null argument");
+    *out = nullptr;
+    c = hb::create_ctx(grid, tables, omega, opts);
+  });
+  if (st != HB_OK) return st;
+  *out = c;
+  return HB_OK;
+}
+
+hb_status hb_save(hb_handle h, const char* path) {
+  return guarded(h, [&] {
+    if (!h || !path) throw hb::arg_error("null argument");
+    if (!h->built) throw hb::Error{HB_ERR_STATE, "hb_save before hb_build"};
+    hb::save_file(h, path);
+  });
+}
+
+hb_status hb_load(const char* path, hb_handle* out) {
+  hb_ctx* c = nullptr;
+  hb_status st = guarded(nullptr, [&] {
+    if (!path || !out) throw hb::arg_error("null argument");
+    *out = nullptr;
+    c = hb::load_file(path, &hb::create_ctx);
+  });
+  if (st != HB_OK) return st;
   *out = c;
   return HB_OK;
 }

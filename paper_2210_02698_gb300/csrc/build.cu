@@ -103,6 +103,8 @@ void form_job(const hb_ctx* c, const std::vector<Butterfly>& bfs, Job& jb, std::
 
 }  // namespace
 
+static void make_plans(hb_ctx* c, std::vector<Butterfly>& bfs, const std::vector<long long>& leaf_off);
+
 void build(hb_ctx* c) {
   const auto t_begin = std::chrono::steady_clock::now();
   const int Lv = c->Lv;
@@ -306,6 +308,43 @@ void build(hb_ctx* c) {
   }
   HB_CUDA(cudaStreamSynchronize(st));
   for (const Segment& s : segs) dev_free(s.ptr);
+
+  // the factor index (what hb_save writes) and the apply plans
+  c->bidx.clear();
+  for (const Butterfly& b : bfs) {
+    BflyIndex x;
+    x.l = b.l;
+    x.oi = b.oi;
+    x.si = b.si;
+    x.L = b.L;
+    x.rank.assign((size_t)b.L + 1, {});
+    x.f_off.assign((size_t)b.L + 1, {});
+    for (int k = 0; k <= b.L; ++k)
+      for (const BlockRec& br : b.lev[(size_t)k]) {
+        x.rank[(size_t)k].push_back(br.rank);
+        x.f_off[(size_t)k].push_back(br.f_off);
+      }
+    x.kl_off = b.kl_off;
+    c->bidx.push_back(std::move(x));
+  }
+  c->leaf_off = leaf_off;
+  make_plans(c, bfs, leaf_off);
+  c->stats.id_blocks = id_blocks;
+  c->stats.sampled_entries = sampled;
+  c->stats.build_ms =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_begin).count();
+}
+
+// Apply plans from the factor index: FP64 step lists, native arenas and the
+// mixed-apply plans of both directions; statistics of the factors.
+static void make_plans(hb_ctx* c, std::vector<Butterfly>& bfs, const std::vector<long long>& leaf_off) {
+  const int Lv = c->Lv;
+  const int Lmax = Lv - 1;
+  cudaStream_t st = 0;
+  int max_rank = 0;
+  for (const Butterfly& b : bfs)
+    for (const auto& lev : b.lev)
+      for (const BlockRec& br : lev) max_rank = std::max(max_rank, br.rank);
 
   // xh offsets (FP64 path: packed rows; native layout: padded row tiles)
   long long xh = 0, xht = 0;
@@ -620,17 +659,35 @@ void build(hb_ctx* c) {
 
   c->max_rank = max_rank;
   c->stats.max_rank = max_rank;
-  c->stats.factor_entries = nfac;
-  c->stats.factor_bytes_fp64 = nfac * (long long)sizeof(double2);
+  c->stats.factor_entries = c->n_factor;
+  c->stats.factor_bytes_fp64 = c->n_factor * (long long)sizeof(double2);
   c->stats.factor_bytes_mixed = c->nat_tiles[0] * 512;
-  c->stats.id_blocks = id_blocks;
-  c->stats.sampled_entries = sampled;
   c->stats.skeleton_rows = c->xh_rows;
   // mixed-precision apply of up to 32 right-hand sides: the gather and one
   // step launch per dependency depth (the last one writes u)
   c->stats.apply_launches = 1 + flow_plan_depths(c->flow_plan[0]);
-  c->stats.build_ms =
-      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_begin).count();
+}
+
+// hb_load: the apply plans of a factor index read from a file (the arena
+// c->d_f64, c->bidx and c->leaf_off are in place).
+void plans_from_index(hb_ctx* c) {
+  std::vector<Butterfly> bfs;
+  for (const BflyIndex& x : c->bidx) {
+    Butterfly b;
+    b.l = x.l;
+    b.oi = x.oi;
+    b.si = x.si;
+    b.L = x.L;
+    b.lev.assign((size_t)x.L + 1, std::vector<BlockRec>((size_t)1 << x.L));
+    for (int k = 0; k <= x.L; ++k)
+      for (size_t j = 0; j < b.lev[(size_t)k].size(); ++j) {
+        b.lev[(size_t)k][j].rank = x.rank[(size_t)k][j];
+        b.lev[(size_t)k][j].f_off = x.f_off[(size_t)k][j];
+      }
+    b.kl_off = x.kl_off;
+    bfs.push_back(std::move(b));
+  }
+  make_plans(c, bfs, c->leaf_off);
 }
 
 }  // namespace hb

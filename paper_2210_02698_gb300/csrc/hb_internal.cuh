@@ -131,6 +131,16 @@ struct NatTask {
   std::vector<NatTerm> terms;
 };
 
+// Factor index of one butterfly (what hb_save writes besides the arena):
+// level-k block (i, j) = rank[k][i 2^(L-k) + j] x (its columns), stored
+// column-major at f_off[k][.] of the FP64 arena; K^L block i at kl_off[i].
+struct BflyIndex {
+  int l, oi, si, L;
+  std::vector<std::vector<int>> rank;
+  std::vector<std::vector<long long>> f_off;
+  std::vector<long long> kl_off;
+};
+
 // Host-side batch of ragged entry blocks (entries.cu).
 struct BlockMeta {
   long long row_off, m, col_off, n, out_off, seg_off, nseg, pad;
@@ -172,6 +182,8 @@ struct hb_ctx {
 
   // build results
   bool built = false;
+  std::vector<hb::BflyIndex> bidx;   // factor index of every butterfly (HODBF order)
+  std::vector<long long> leaf_off;   // dense leaf blocks in the FP64 arena
   hb_stats stats{};
   // FP64 factor arena (double2, column-major blocks)
   long long n_factor = 0;
@@ -225,6 +237,10 @@ void emit_v(int count, const int* d_m, const int* d_n, const long long* d_aoff, 
             const int* d_rank, const int* d_perm, const long long* d_soff, const long long* d_voff,
             int ld_is_rank, double2* V64, float2* V32, cudaStream_t st);
 void build(hb_ctx* c);
+void plans_from_index(hb_ctx* c);                      // build.cu: hb_load
+void save_file(const hb_ctx* c, const char* path);     // io.cu
+hb_ctx* load_file(const char* path,
+                  hb_ctx* (*create)(const hb_grid*, const hb_tables*, double, const hb_options*));
 void id_batch_noalloc(int count, const int* m, const int* n, const long long* a_off, double2* A, double eps,
                       int* rank, int* skel, double2* V, cudaStream_t st);
 void flow_plan_build(const std::vector<NatTask>& tasks, void** plan_out);
