@@ -263,6 +263,11 @@ def run_ours(args):
     apply64 = lambda: op.apply(s_dev, u_dev, R, stream)  # noqa: E731
     ms64 = timed(apply64, max(3, args.steps // 4), 2)
     u64 = u_dev.clone()
+
+    # ---- plain FP64 GPU matrix-free dense sum (every entry evaluated on the fly)
+    u_dense = torch.empty_like(u_dev)
+    apply_dense = lambda: op.apply_dense(s_dev, u_dense, R, stream)  # noqa: E731
+    ms_dense = timed(apply_dense, 1, 1)
     op.set_precision(binding.HB_MIXED_BF16X3)
 
     # ---- end to end through the public API with host buffers
@@ -311,6 +316,26 @@ def run_ours(args):
                    "rel_l2_fp64_vs_oracle": float(np.linalg.norm(got64 - U_ref) / np.linalg.norm(U_ref))}
         except Exception as ex:  # the baseline must never break the bench line
             cpu = {"value": None, "unit": UNIT, "cores": nc, "kind": "oracle", "sample": f"failed: {ex}"}
+        # the oracle's CPU butterfly apply over the saved factors (all rows, all RHS)
+        cpu_bf = {}
+        try:
+            if args.skip_cpu:
+                raise RuntimeError("skipped (--skip-cpu)")
+            from oracle.factor_file import FactorFile
+            with tempfile.TemporaryDirectory() as td:
+                path = os.path.join(td, "op.hbf")
+                op.save(path)
+                F = FactorFile(path)
+            t0 = time.perf_counter()
+            u_cpu = F.apply(s_host)
+            dt = time.perf_counter() - t0
+            cpu_bf = {"value": Nv * R / dt, "unit": UNIT, "cores": nc, "kind": "oracle",
+                      "sample": f"full FP64 butterfly apply of the saved factors, {Nv} rows x {R} RHS "
+                                f"({dt:.1f} s, numpy)",
+                      "rel_l2_fp64_gpu_vs_cpu_butterfly":
+                          float(np.linalg.norm(u64.cpu().numpy().T - u_cpu) / np.linalg.norm(u_cpu))}
+        except Exception as ex:
+            cpu_bf = {"value": None, "unit": UNIT, "cores": nc, "kind": "oracle", "sample": f"failed: {ex}"}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -331,7 +356,11 @@ def run_ours(args):
             "gpu_launches": info["apply_launches"] * args.steps,
             "clocks": clk,
             "cpu_baseline": cpu,
+            "cpu_butterfly": cpu_bf,
             "fp64_gpu": {"value": Nv * R * world / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64},
+            "fp64_gpu_dense": {"value": Nv * R * world / (ms_dense * 1e-3), "unit": UNIT, "ms_per_step": ms_dense,
+                               "rel_l2_mixed_vs_dense": float(torch.linalg.norm(u_mixed - u_dense)
+                                                              / torch.linalg.norm(u_dense))},
             "speedup_vs_fp64_gpu": ms64 / ms,
             "rel_l2_mixed_vs_fp64_butterfly": rel_mixed_fp64,
             "build_s": build_s,
