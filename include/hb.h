@@ -84,9 +84,9 @@ typedef struct {
  * the start of each kernel) of the bounded device waits of the mixed apply
  * (0 = default, 2^31).  A wait that runs out sets a mapped error word; the
  * kernel then lets its copies in flight land (waiting at least 2^31 cycles
- * for them) and stops, and the next hb_apply / hb_apply_adjoint on the
- * handle returns HB_ERR_TIMEOUT (the outputs of the apply that ran out are
- * undefined). */
+ * for them) and stops; a later hb_apply / hb_apply_adjoint on the handle,
+ * called once the device has run the apply that ran out, returns
+ * HB_ERR_TIMEOUT (the outputs of the apply that ran out are undefined). */
 typedef struct {
   double eps;
   int leaf;
@@ -178,8 +178,9 @@ hb_status hb_set_precision(hb_handle h, int precision);
  * launch of later mixed applies also waits - with the same bounded wait as
  * the data waits and the handle's barrier_cycles budget - on an mbarrier
  * that nothing completes; the wait runs out and sets the mapped error word,
- * and the apply otherwise completes normally, so the next hb_apply /
- * hb_apply_adjoint returns HB_ERR_TIMEOUT.  No fault or hang is involved;
+ * and the apply otherwise completes normally, so a later hb_apply /
+ * hb_apply_adjoint (called after the device has run it) returns
+ * HB_ERR_TIMEOUT.  No fault or hang is involved;
  * each launch spends about barrier_cycles SM cycles in the wait.
  * Errors: HB_ERR_ARG for a null handle. */
 hb_status hb_set_wait_selftest(hb_handle h, int on);

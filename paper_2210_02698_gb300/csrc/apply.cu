@@ -156,30 +156,39 @@ struct TimerScope {
   }
 };
 
-void ensure_scratch(hb_ctx* c, int nrhs) {
-  if (c->cap_rhs >= nrhs) return;
-  dev_free(c->d_x);
-  dev_free(c->d_y);
-  dev_free(c->d_xh);
-  c->d_x = c->d_y = c->d_xh = nullptr;
-  c->cap_rhs = 0;
-  // one spare row: 1D bulk copies round their size up to 16 bytes
-  c->d_x = dev_alloc<double2>((size_t)(c->Nv + 1) * nrhs);
-  c->d_y = dev_alloc<double2>((size_t)(c->Nv + 1) * nrhs);
-  c->d_xh = dev_alloc<double2>((size_t)(std::max<long long>(c->xh_rows, 1) + 1) * nrhs);
-  c->cap_rhs = nrhs;
-  if (!c->d_perm) c->d_perm = upload(c->perm);
-  if (!c->d_mx) {
+// Scratch of the precision in use (allocated on first use, kept); the device
+// is synchronised only after an allocation, so applies stay asynchronous.
+void ensure_scratch(hb_ctx* c, int nrhs, bool fp64) {
+  bool fresh = false;
+  if (fp64 && c->cap_rhs < nrhs) {
+    fresh = true;
+    dev_free(c->d_x);
+    dev_free(c->d_y);
+    dev_free(c->d_xh);
+    c->d_x = c->d_y = c->d_xh = nullptr;
+    c->cap_rhs = 0;
+    c->d_x = dev_alloc<double2>((size_t)(c->Nv + 1) * nrhs);
+    c->d_y = dev_alloc<double2>((size_t)(c->Nv + 1) * nrhs);
+    c->d_xh = dev_alloc<double2>((size_t)(std::max<long long>(c->xh_rows, 1) + 1) * nrhs);
+    c->cap_rhs = nrhs;
+  }
+  if (!c->d_perm) {
+    fresh = true;
+    c->d_perm = upload(c->perm);
+  }
+  if (!fp64 && !c->d_mx) {
     // native vectors for two m-tiles: 2 KB per row tile
+    fresh = true;
     c->d_mx = dev_alloc<uint4>((size_t)std::max<long long>(c->nv_tiles, 1) * 128);
     c->d_mxh = dev_alloc<uint4>((size_t)std::max<long long>(c->xh_tiles, 1) * 128);
   }
   if (!c->h_err) {
+    fresh = true;
     HB_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&c->h_err), sizeof(int), cudaHostAllocMapped));
     *c->h_err = 0;
     HB_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void**>(&c->d_err), c->h_err, 0));
   }
-  HB_CUDA(cudaDeviceSynchronize());
+  if (fresh) HB_CUDA(cudaDeviceSynchronize());
 }
 
 template <class C>
@@ -202,8 +211,10 @@ void apply_bf(hb_ctx* c, const double2* s, double2* u, int nrhs, int adjoint, in
     *reinterpret_cast<volatile int*>(c->h_err) = 0;
     throw Error{HB_ERR_TIMEOUT, "a bounded device wait of an earlier apply gave up"};
   }
-  const int chunk = (precision == HB_FP64) ? nrhs : std::min(nrhs, 32);
-  ensure_scratch(c, chunk);
+  // right-hand sides per pass: the scratch vectors (skeleton rows x pass x 16
+  // bytes for FP64) stay bounded for any nrhs
+  const int chunk = std::min(nrhs, precision == HB_FP64 ? 16 : 32);
+  ensure_scratch(c, chunk, precision == HB_FP64);
   TimerScope ts{c, st, {}};
   const double scale = c->h * c->h;
   for (int r0 = 0; r0 < nrhs; r0 += chunk) {

@@ -565,11 +565,18 @@ struct DepthStreams {
   long long* d_off = nullptr;
 };
 
+struct LaunchShape {   // per m-tile count, set on first use
+  bool ready = false;
+  int stage = 0, stages = 0, grid = 0;
+  size_t smem = 0;
+};
+
 struct FlowPlan {
   // chains of every depth: the items of one chain, in order
   std::vector<std::vector<std::vector<WItem>>> chains;
   int stage_bytes[3] = {0, 512, 512};     // largest item at MT = 1, 2
   int grid = 0;                           // CTAs the streams were dealt for
+  LaunchShape shape[3];
   std::vector<DepthStreams> streams;
 };
 
@@ -698,31 +705,39 @@ static void launch_depths(FlowPlan* P, const uint4* F, uint4* x, uint4* xh, doub
                           long long Nv, int R, int* err, long long budget, bool selftest, cudaStream_t st,
                           const std::function<void(int, bool)>& timer) {
   auto k = bf_step_kernel<MT>;
-  int dev = 0, nsm = 0, optin = 0;
-  HB_CUDA(cudaGetDevice(&dev));
-  HB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  HB_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  cudaFuncAttributes fa{};
-  HB_CUDA(cudaFuncGetAttributes(&fa, k));
-  const int stage = P->stage_bytes[MT];
-  const int avail = optin - (int)fa.sharedSizeBytes;
-  const int stages = std::min(MAX_STAGES, avail / (NWARP * stage));
-  if (stages < 2) throw Error{HB_ERR_UNSUPPORTED, "step kernel stages do not fit in shared memory"};
-  const size_t smem = (size_t)NWARP * stages * stage;
-  HB_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int per_sm = 0;
-  HB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NWARP * 32, smem));
-  if (per_sm < 1) throw Error{HB_ERR_UNSUPPORTED, "step kernel does not fit on an SM"};
-  if (P->grid != nsm * per_sm) build_streams(P, nsm * per_sm);
+  LaunchShape& L = P->shape[MT];
+  if (!L.ready) {
+    // once per plan and m-tile count: stages, shared memory, grid (then the streams)
+    int dev = 0, nsm = 0, optin = 0;
+    HB_CUDA(cudaGetDevice(&dev));
+    HB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    HB_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cudaFuncAttributes fa{};
+    HB_CUDA(cudaFuncGetAttributes(&fa, k));
+    L.stage = P->stage_bytes[MT];
+    const int avail = optin - (int)fa.sharedSizeBytes;
+    L.stages = std::min(MAX_STAGES, avail / (NWARP * L.stage));
+    if (L.stages < 2) throw Error{HB_ERR_UNSUPPORTED, "step kernel stages do not fit in shared memory"};
+    L.smem = (size_t)NWARP * L.stages * L.stage;
+    // the kernel may take any size up to the opt-in limit (both directions' plans share it)
+    HB_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, avail));
+    int per_sm = 0;
+    HB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NWARP * 32, L.smem));
+    if (per_sm < 1) throw Error{HB_ERR_UNSUPPORTED, "step kernel does not fit on an SM"};
+    L.grid = nsm * per_sm;
+    L.ready = true;
+  }
+  if (P->grid != L.grid) build_streams(P, L.grid);
   bool first = true;   // the timer brackets all depth launches (PDL stays intact)
   for (int d = 0; d < (int)P->streams.size(); ++d) {
     const DepthStreams& ds = P->streams[(size_t)d];
     if (ds.grid == 0) continue;
-    StepArgs args{ds.d_items, ds.d_off, F, x, xh, u, pperm, Nv, R, stages, stage, budget, err, selftest ? 1 : 0};
+    StepArgs args{ds.d_items, ds.d_off, F, x, xh, u, pperm, Nv, R, L.stages, L.stage, budget, err,
+                  selftest ? 1 : 0};
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(ds.grid);
     cfg.blockDim = dim3(NWARP * 32);
-    cfg.dynamicSmemBytes = smem;
+    cfg.dynamicSmemBytes = L.smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
