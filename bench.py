@@ -41,6 +41,13 @@ METRIC = "HB butterfly apply N_v·RHS/s at rel-L2≤1e-4, % roofline, vs plain F
 UNIT = "N_v*RHS/s"
 
 
+def describe(w):
+    """The workload as a config string: medium, grid, frequency, tables, tolerance, sources."""
+    med = {"grad": "c=1+0.5z", "homog": "n=1"}.get(w.medium.key.split("_")[0], w.medium.key)
+    return (f"{w.name}: {med}, {w.N}x{w.N} cells (N_v={w.grid.Nv}), omega=2pi*{w.omega / (2 * math.pi):g}, "
+            f"n_I={w.n_I}, eps={w.eps:g}, chi={w.chi:g}, leaf {w.leaf}, {w.nrhs} RHS ({w.rhs_kind})")
+
+
 def table_path(w):
     return os.path.join(ROOT, "tests", "golden", "tables", f"{w.medium.key}_nI{w.n_I}.npz")
 
@@ -183,8 +190,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "grad256: c=1+0.5z, 256x256 cells, omega=2pi*32, n_I=16, 16 complex "
-                                   "Gaussian RHS", "sample": f"{rows_per_step} seeded output rows x all "
+            "config": {"workload": describe(w), "sample": f"{rows_per_step} seeded output rows x all "
                                    f"{w.grid.Nv} sources x {w.nrhs} RHS per step"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": nc, "kind": "oracle",
                              "sample": f"dense HB sum (numpy/scipy FP64) on {rows_per_step} rows per step"},
@@ -262,7 +268,14 @@ def run_ours(args):
         graph_note = f"graph capture failed: {ex}"
     ms = ms_graph if ms_graph is not None else ms_eager
     clk = clocks.stop()
-    u_mixed = u_dev.clone()
+    # large problems keep no full extra copies of the vectors on the device:
+    # the rel-L2 checks use the oracle's row sample there
+    large = Nv * R > (1 << 24)
+    rows_n = 384 if Nv <= (1 << 18) else max(8, 384 * 65536 // Nv)   # ~10-15 s of the oracle
+    rows = W.sample_rows(Nv, rows_n, 1234)
+    rows_t = torch.from_numpy(rows).to(dev)
+    mixed_rows = u_dev[:, rows_t].cpu().numpy().T
+    u_mixed = None if large else u_dev.clone()
     # per-kernel-group device time of one apply (events on the launch stream)
     op.set_kernel_timing(True)
     ktimes = {}
@@ -276,28 +289,34 @@ def run_ours(args):
     op.set_precision(binding.HB_FP64)
     apply64 = lambda: op.apply(s_dev, u_dev, R, stream)  # noqa: E731
     ms64 = timed(apply64, max(3, args.steps // 4), 2)
-    u64 = u_dev.clone()
+    fp64_rows = u_dev[:, rows_t].cpu().numpy().T
+    if large:
+        rel_mixed_fp64 = float(np.linalg.norm(mixed_rows - fp64_rows) / np.linalg.norm(fp64_rows))
+    else:
+        rel_mixed_fp64 = float(torch.linalg.norm(u_mixed - u_dev) / torch.linalg.norm(u_dev))
+    u64_host = None if large else u_dev.cpu().numpy().T
 
     # ---- plain FP64 GPU matrix-free dense sum (every entry evaluated on the fly)
-    u_dense = torch.empty_like(u_dev)
-    apply_dense = lambda: op.apply_dense(s_dev, u_dense, R, stream)  # noqa: E731
-    ms_dense = timed(apply_dense, 1, 1)
+    dense_line = {"value": None, "unit": UNIT, "note": "skipped at this size (seconds per entry batch)"}
+    if not large:
+        apply_dense = lambda: op.apply_dense(s_dev, u_dev, R, stream)  # noqa: E731
+        ms_dense = timed(apply_dense, 1, 1)
+        dense_line = {"value": Nv * R * world / (ms_dense * 1e-3), "unit": UNIT, "ms_per_step": ms_dense,
+                      "rel_l2_mixed_vs_dense": float(torch.linalg.norm(u_mixed - u_dev) / torch.linalg.norm(u_dev))}
     op.set_precision(binding.HB_MIXED_BF16X3)
+    u_mixed = None
 
     # ---- end to end through the public API with host buffers
     s_pin = torch.from_numpy(np.ascontiguousarray(s_host.T)).pin_memory()
     u_pin = torch.empty_like(s_pin).pin_memory()
-    s_stage = torch.empty_like(s_dev)
 
     def e2e():
-        s_stage.copy_(s_pin, non_blocking=True)
-        op.apply(s_stage, u_dev, R, stream)
+        s_dev.copy_(s_pin, non_blocking=True)      # s_dev is the staging buffer (same values)
+        op.apply(s_dev, u_dev, R, stream)
         u_pin.copy_(u_dev, non_blocking=True)
 
     ms_e2e = timed(e2e, args.steps, 2)
 
-    # ---- rel-L2 of mixed vs FP64 butterfly (device) and vs the dense FP64 GPU sum on sampled rows
-    rel_mixed_fp64 = float(torch.linalg.norm(u_mixed - u64) / torch.linalg.norm(u64))
     result = {}
     if rank == 0:
         hbm, peak_kind = peaks()
@@ -316,13 +335,12 @@ def run_ours(args):
         # cpu baseline: oracle dense sum on a bounded row sample, plus the
         # rel-L2 of our mixed output on those rows
         cpu = {}
-        rows_n = 384   # about 15 s of the oracle on the host cores
         try:
             if args.skip_cpu:
                 raise RuntimeError("skipped (--skip-cpu)")
-            rows, U_ref, dt = cpu_oracle_sample(w, tab, rows_n)
-            got = u_mixed.cpu().numpy().T[rows]
-            got64 = u64.cpu().numpy().T[rows]
+            rows2, U_ref, dt = cpu_oracle_sample(w, tab, rows_n)
+            assert np.array_equal(rows2, rows)
+            got, got64 = mixed_rows, fp64_rows
             cpu = {"value": rows_n * R / dt, "unit": UNIT, "cores": nc, "kind": "oracle",
                    "sample": f"dense FP64 HB sum, {rows_n} seeded rows x {Nv} sources x {R} RHS "
                              f"({dt:.1f} s)",
@@ -335,6 +353,8 @@ def run_ours(args):
         try:
             if args.skip_cpu:
                 raise RuntimeError("skipped (--skip-cpu)")
+            if large:
+                raise RuntimeError("skipped at this size (the factor file would be too large)")
             from oracle.factor_file import FactorFile
             with tempfile.TemporaryDirectory() as td:
                 path = os.path.join(td, "op.hbf")
@@ -347,15 +367,14 @@ def run_ours(args):
                       "sample": f"full FP64 butterfly apply of the saved factors, {Nv} rows x {R} RHS "
                                 f"({dt:.1f} s, numpy)",
                       "rel_l2_fp64_gpu_vs_cpu_butterfly":
-                          float(np.linalg.norm(u64.cpu().numpy().T - u_cpu) / np.linalg.norm(u_cpu))}
+                          float(np.linalg.norm(u64_host - u_cpu) / np.linalg.norm(u_cpu))}
         except Exception as ex:
             cpu_bf = {"value": None, "unit": UNIT, "cores": nc, "kind": "oracle", "sample": f"failed: {ex}"}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-            "config": {"workload": "grad256: c=1+0.5z, 256x256 cells (N_v=65536), omega=2pi*32, n_I=16, "
-                                   "eps=1e-6, chi=20, leaf 64, 16 complex Gaussian RHS",
+            "config": {"workload": describe(w),
                        "l2": f"factors {fac_bytes / 2**20:.0f} MiB > 129 MB L2, no flush",
                        "precision": "factors and vectors as split-BF16 pairs (hi + lo), three BF16 "
                                     "tensor-core products per complex MAC, FP32 accumulate, FP64 output",
@@ -374,13 +393,14 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "cpu_butterfly": cpu_bf,
             "fp64_gpu": {"value": Nv * R * world / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64},
-            "fp64_gpu_dense": {"value": Nv * R * world / (ms_dense * 1e-3), "unit": UNIT, "ms_per_step": ms_dense,
-                               "rel_l2_mixed_vs_dense": float(torch.linalg.norm(u_mixed - u_dense)
-                                                              / torch.linalg.norm(u_dense))},
+            "fp64_gpu_dense": dense_line,
             "speedup_vs_fp64_gpu": ms64 / ms,
             "rel_l2_mixed_vs_fp64_butterfly": rel_mixed_fp64,
+            "rel_l2_scope": f"oracle row sample ({rows_n} rows)" if large else "all rows",
             "build_s": build_s,
             "factor_entries": E,
+            "factor_bytes": {"fp64": info["factor_bytes_fp64"], "mixed_per_direction": info["factor_bytes_mixed"],
+                             "total_device": info["factor_bytes_fp64"] + 2 * info["factor_bytes_mixed"]},
             "max_rank": info["max_rank"],
             "kernel_ms_per_apply": {k: v[0] / nk for k, v in ktimes.items()},
             "gather_scatter_ms": gather_ms,

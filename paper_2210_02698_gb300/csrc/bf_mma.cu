@@ -571,27 +571,34 @@ struct LaunchShape {   // per m-tile count, set on first use
   size_t smem = 0;
 };
 
+// Everything below is kept per m-tile count MT (index 1 or 2): the items are
+// cut so that NWARP warps x 2 stages of the largest item fit in shared memory.
 struct FlowPlan {
   // chains of every depth: the items of one chain, in order
-  std::vector<std::vector<std::vector<WItem>>> chains;
-  int stage_bytes[3] = {0, 512, 512};     // largest item at MT = 1, 2
-  int grid = 0;                           // CTAs the streams were dealt for
+  std::vector<std::vector<std::vector<WItem>>> chains[3];
+  int stage_bytes[3] = {0, 512, 512};     // largest item (factor run + input run)
+  int grid[3] = {0, 0, 0};                // CTAs the streams were dealt for
   LaunchShape shape[3];
-  std::vector<DepthStreams> streams;
+  std::vector<DepthStreams> streams[3];
 };
 
-// k-steps per item for groups of ntl n-tiles: ITEM_BYTES holds the factor
-// run and the input run at two m-tiles.
-static int item_ks(int ntl) { return std::max(1, ITEM_BYTES / (512 * ntl + 2048)); }
+// k-steps per item for groups of ntl n-tiles: at one m-tile, ITEM_BYTES
+// bounds the factor run plus the input run counted at two m-tiles (so an
+// item is at most 12 KB); at two m-tiles the bound is 14 KB (8 warps x 2
+// stages fit in 227 KB).
+static int item_ks(int ntl, int MT) {
+  return std::max(1, (MT == 1 ? ITEM_BYTES : 14336) / (512 * ntl + 2048));
+}
 
-// The chains of one task: group g holds n-tiles [g ng, g ng + ntl); each
-// term contributes its k-steps in runs of at most item_ks(ntl).
-static void task_chains(const NatTask& L, std::vector<std::vector<WItem>>& out, int (&stage_bytes)[3]) {
+// The chains of one task for MT m-tiles: group g holds n-tiles
+// [g ng, g ng + ntl); each term contributes its k-steps in runs of at most
+// item_ks(ntl, MT).
+static void task_chains(const NatTask& L, int MT, std::vector<std::vector<WItem>>& out, int& stage_bytes) {
   if (L.ng < 1 || L.ng > NTW) throw Error{HB_ERR_UNSUPPORTED, "n-tile group larger than the accumulators"};
   const int ngr = (L.nt + L.ng - 1) / L.ng;
   for (int g = 0; g < ngr; ++g) {
     const int ntl = std::min(L.ng, L.nt - g * L.ng);
-    const int kc = item_ks(ntl);
+    const int kc = item_ks(ntl, MT);
     std::vector<WItem> ch;
     for (const NatTerm& tm : L.terms)
       for (int k0 = 0; k0 < tm.ks; k0 += kc) {
@@ -604,8 +611,7 @@ static void task_chains(const NatTask& L, std::vector<std::vector<WItem>>& out, 
         w.x_buf = (unsigned char)tm.x_buf;
         w.y_buf = (unsigned char)L.y_buf;
         ch.push_back(w);
-        for (int mt = 1; mt <= 2; ++mt)
-          stage_bytes[mt] = std::max(stage_bytes[mt], ntl * (int)w.ks * 512 + (int)w.ks * mt * 1024);
+        stage_bytes = std::max(stage_bytes, ntl * (int)w.ks * 512 + (int)w.ks * MT * 1024);
       }
     if (ch.empty()) {   // every input is empty: the group is zero
       WItem w{};
@@ -625,9 +631,11 @@ void flow_plan_build(const std::vector<NatTask>& lt, void** plan_out) {
   try {
     int maxd = -1;
     for (const NatTask& L : lt) maxd = std::max(maxd, L.depth);
-    P->chains.assign((size_t)(maxd + 1), {});
-    for (const NatTask& L : lt)
-      if (L.nt > 0) task_chains(L, P->chains[(size_t)L.depth], P->stage_bytes);
+    for (int mt = 1; mt <= 2; ++mt) {
+      P->chains[mt].assign((size_t)(maxd + 1), {});
+      for (const NatTask& L : lt)
+        if (L.nt > 0) task_chains(L, mt, P->chains[mt][(size_t)L.depth], P->stage_bytes[mt]);
+    }
   } catch (...) {
     delete P;
     throw;
@@ -646,22 +654,23 @@ static void free_streams(std::vector<DepthStreams>& ss) {
 void flow_plan_free(void* plan) {
   FlowPlan* P = static_cast<FlowPlan*>(plan);
   if (!P) return;
-  free_streams(P->streams);
+  for (auto& ss : P->streams) free_streams(ss);
   delete P;
 }
 
-int flow_plan_depths(const void* plan) { return (int)static_cast<const FlowPlan*>(plan)->chains.size(); }
+int flow_plan_depths(const void* plan) { return (int)static_cast<const FlowPlan*>(plan)->chains[1].size(); }
 
 // Deal every depth's chains over grid x NWARP warp streams: longest chain
 // (in factor tiles, plus a fixed cost per item) first, to the stream with
 // the least work so far.
-static void build_streams(FlowPlan* P, int grid) {
-  free_streams(P->streams);
+static void build_streams(FlowPlan* P, int grid, int MT) {
+  std::vector<DepthStreams>& out = P->streams[MT];
+  free_streams(out);
   const int ns = grid * NWARP;
-  for (const auto& chains : P->chains) {
+  for (const auto& chains : P->chains[MT]) {
     DepthStreams ds;
     if (chains.empty()) {
-      P->streams.push_back(ds);
+      out.push_back(ds);
       continue;
     }
     std::vector<long long> cost(chains.size());
@@ -694,10 +703,10 @@ static void build_streams(FlowPlan* P, int grid) {
     ds.grid = grid;
     ds.d_items = upload(items);
     ds.d_off = upload(off);
-    P->streams.push_back(ds);
+    out.push_back(ds);
   }
   HB_CUDA(cudaDeviceSynchronize());
-  P->grid = grid;
+  P->grid[MT] = grid;
 }
 
 template <int MT>
@@ -727,10 +736,10 @@ static void launch_depths(FlowPlan* P, const uint4* F, uint4* x, uint4* xh, doub
     L.grid = nsm * per_sm;
     L.ready = true;
   }
-  if (P->grid != L.grid) build_streams(P, L.grid);
+  if (P->grid[MT] != L.grid) build_streams(P, L.grid, MT);
   bool first = true;   // the timer brackets all depth launches (PDL stays intact)
-  for (int d = 0; d < (int)P->streams.size(); ++d) {
-    const DepthStreams& ds = P->streams[(size_t)d];
+  for (int d = 0; d < (int)P->streams[MT].size(); ++d) {
+    const DepthStreams& ds = P->streams[MT][(size_t)d];
     if (ds.grid == 0) continue;
     StepArgs args{ds.d_items, ds.d_off, F, x, xh, u, pperm, Nv, R, L.stages, L.stage, budget, err,
                   selftest ? 1 : 0};
@@ -755,7 +764,7 @@ void flow_launch(void* plan, const uint4* F, uint4* x, uint4* xh, double2* u, co
                  int R, int* err, long long budget_cycles, bool selftest, cudaStream_t st,
                  const std::function<void(int, bool)>& timer) {
   FlowPlan* P = static_cast<FlowPlan*>(plan);
-  if (P->chains.empty()) return;
+  if (P->chains[1].empty()) return;
   const int MT = (R + 15) / 16;
   if (MT == 1) launch_depths<1>(P, F, x, xh, u, pperm, Nv, R, err, budget_cycles, selftest, st, timer);
   else if (MT == 2) launch_depths<2>(P, F, x, xh, u, pperm, Nv, R, err, budget_cycles, selftest, st, timer);

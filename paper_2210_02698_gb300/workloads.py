@@ -128,6 +128,8 @@ WORKLOADS = {
     # Source inversion workload of the gradient medium at 512^2.
     "grad512": Workload("grad512", 512, GRADIENT, 2 * math.pi * 64, 16, 1),
     # Large constant-gradient workload, 256 wavelengths across, 128 sources.
+    # Intermediate constant-gradient size (scaling between 512^2 and 2048^2).
+    "grad1024": Workload("grad1024", 1024, GRADIENT, 2 * math.pi * 128, 16, 32),
     "grad2048": Workload("grad2048", 2048, GRADIENT, 2 * math.pi * 256, 16, 128),
 }
 
