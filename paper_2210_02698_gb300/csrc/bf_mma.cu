@@ -522,6 +522,9 @@ __global__ void __launch_bounds__(256) gather_native_kernel(const double2* __res
                                                             uint4* __restrict__ x, long long nv_tiles, long long Nv,
                                                             int R, int MT, double scale) {
   __shared__ __align__(16) uint32_t tile[8][256];
+  // the first depth launch may start now and stream its factor runs; it
+  // reads x only after griddepcontrol.wait, i.e. after this grid completes
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
   const long long wid = (long long)blockIdx.x * 8 + wb;
   if (wid >= nv_tiles * MT) return;
