@@ -14,7 +14,12 @@ Modules (each function cites the passage it follows):
 * ``tables``    - the tabulated ingredients tau^2, v0, v1 at node pairs
   (Sec. 2, Eq. eikonal, Eq. equVs, Eq. initialv0; Sec. 5.1.1 media).
 * ``taylor``    - the near-source Taylor recursions (Sec. 2.2, Eq. recursiveT,
-  Eq. recursiveB, Eq. C0, Eq. C1); used to pin ``tables``.
+  Eq. recursiveB, Eq. C0, Eq. C1); used to pin ``tables`` and to start
+  ``sweep``.
+* ``sweep``     - Lax-Friedrichs WENO sweeping for the factored eikonal and
+  the transport equations (Sec. 2.3, Eq. faceik, Eq. equVs) on a mesh, for
+  media without closed-form ingredients (the Gaussian lens); numerics in
+  plain C (``sweep.c``, compiled with gcc on first use).
 * ``hankel``    - the Hankel-type functions f_q (Eq. termf).
 * ``kernel``    - matrix entries g = v0 f0 + v1 f1 (Eq. babich) and the 2D
   self term (Appendix A, Eq. HankelIntegral2dlemma).

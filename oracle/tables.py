@@ -144,7 +144,7 @@ def ingredient_functions(medium):
             return t * t, v0_gradient(t, g), v1_gradient(t, g).reshape(np.shape(t))
         return f
     raise NotImplementedError(
-        f"no table builder for medium kind {medium.kind!r} in the oracle")
+        f"no exact ingredients for medium kind {medium.kind!r}: use oracle.sweep.build_tables")
 
 
 def build_tables(medium, n_I: int):

@@ -1,0 +1,126 @@
+"""Pins of the oracle's sweeping table builder (oracle/sweep.py, sweep.c;
+Sec. 2.3: factored eikonal Eq. faceik and transport Eq. equVs by
+Lax-Friedrichs WENO sweeping, Taylor initialisation Eq. expansionT /
+expansionV0 / expansionV1, local cubic interpolation to the nodes).
+
+* Constant-gradient medium, whose tau, v0, v1 are exact in oracle.tables:
+  the mesh errors over the unit square fall at least at the orders the
+  paper states for tau, v0, v1 (fifth, third, first in h0), for an interior
+  source and a corner source; tables at h0 = 1/64 match the exact tables.
+* Homogeneous medium: the sweeps keep the exact solution tau = n0 |r - r0|,
+  v0 = B0, v1 = 0.
+* Lens: the series n^2 = sum S_k about a source has an O(rho^5) remainder;
+  the stored lens tables are reciprocal (tau^2, v0, v1 symmetric in
+  observation and source node), invariant under the lens's symmetries
+  (x -> 1 - x, z -> 1 - z, x <-> z: the medium and the node set are), v0
+  stays positive (no caustic), and the eikonal and v0 solves converged.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import chebyshev, sweep, tables
+from paper_2210_02698_gb300 import workloads as W
+from tests._common import load_tables, table_path
+
+B0 = 1.0 / (2.0 * math.sqrt(math.pi))
+
+
+def _errors(medium, x0, z0, h0):
+    t2, v0, v1, X, Z, info = sweep.fields(medium, x0, z0, h0)
+    et2, ev0, ev1 = tables.ingredient_functions(medium)(X, Z, x0, z0)
+    ins = (X >= 0) & (X <= 1) & (Z >= 0) & (Z <= 1)
+    return (np.abs(np.sqrt(t2) - np.sqrt(et2))[ins].max(), np.abs(v0 - ev0)[ins].max(),
+            np.abs(v1 - ev1)[ins].max(), info)
+
+
+@pytest.mark.parametrize("src", ["interior", "corner"])
+def test_gradient_medium_convergence_orders(src):
+    xn = chebyshev.nodes(16)
+    x0, z0 = (0.3141, 0.4472) if src == "interior" else (xn[0], xn[15])
+    e1 = _errors(W.GRADIENT, x0, z0, 1 / 32)
+    e2 = _errors(W.GRADIENT, x0, z0, 1 / 64)
+    for info in (e1[3], e2[3]):
+        assert np.all(info[3:] < 1e-12)                  # every solve converged
+    # orders >= 4.5, 3, 1 over one halving (the paper: 5, 3, 1)
+    assert e1[0] / e2[0] > 2 ** 4.5 and e2[0] < 2e-9
+    assert e1[1] / e2[1] > 2 ** 3 and e2[1] < 5e-8
+    assert e1[2] / e2[2] > 2 ** 1 and e2[2] < 2e-5
+
+
+def test_gradient_tables_match_exact():
+    src = np.array([0, 37, 120, 255])
+    t = sweep.build_tables(W.GRADIENT, 16, h0=1 / 64, sources=src)
+    ex = tables.build_tables(W.GRADIENT, 16)
+    assert np.abs(t["tau2"] - ex["tau2"][:, src]).max() < 5e-8
+    assert np.abs(t["v0"] - ex["v0"][:, src]).max() < 5e-7
+    assert np.abs(t["v1"] - ex["v1"][:, src]).max() < 1e-4
+    assert np.all(t["info"][:, 3:] < 1e-12)
+
+
+def test_homogeneous_medium_is_a_fixed_point():
+    med = W.Medium("homogeneous", n0=1.3)
+    x0, z0 = 0.4, 0.7
+    t2, v0, v1, X, Z, info = sweep.fields(med, x0, z0, 1 / 32)
+    ins = np.isfinite(v0)
+    assert np.abs(t2 - 1.3 ** 2 * ((X - x0) ** 2 + (Z - z0) ** 2)).max() < 1e-12
+    assert np.abs(v0[ins] - B0).max() < 1e-12
+    assert np.abs(v1[ins]).max() < 1e-11        # Lap v0 of a constant: rounding / h0^2
+
+
+def test_lens_n2_series_remainder():
+    med = W.LENS
+    x0, z0 = 0.31, 0.62
+    S = sweep.n2_series(med, x0, z0, 4)
+    rng = np.random.default_rng(3)
+    th = rng.uniform(0, 2 * np.pi, 16)
+    errs = []
+    for rho in (0.04, 0.02):
+        X, Z = rho * np.cos(th), rho * np.sin(th)
+        approx = sum(np.sum([c * X ** (k - m) * Z ** m for m, c in enumerate(S[k])], axis=0) for k in range(5))
+        exact = med.n(x0 + X, z0 + Z) ** 2
+        errs.append(np.abs(approx - exact).max())
+    assert errs[0] / errs[1] > 2 ** 4.7                   # remainder O(rho^5)
+
+
+def _lens():
+    return load_tables(W.LENS), np.load(table_path(W.LENS))["sweep_info"]
+
+
+def _node_maps(n_I=16):
+    i1, i2 = np.meshgrid(np.arange(n_I), np.arange(n_I))
+    i1, i2 = i1.reshape(-1), i2.reshape(-1)          # node k = i2 n_I + i1
+    flip_x = i2 * n_I + (n_I - 1 - i1)
+    flip_z = (n_I - 1 - i2) * n_I + i1
+    swap = i1 * n_I + i2
+    return flip_x, flip_z, swap
+
+
+def test_lens_tables_reciprocity_symmetry_positivity():
+    t, info = _lens()
+    assert np.all(info[:, 3] < 1e-11) and np.all(info[:, 4] < 1e-11)   # eikonal, v0 converged
+    v1max = np.abs(t["v1"]).max()
+    assert np.all(info[:, 5] < 1e-3 * v1max)                            # v1: last update small
+    idx = np.arange(256)
+    assert np.all(t["tau2"][idx, idx] == 0.0) and np.all(t["v0"][idx, idx] == B0)
+    assert t["v0"].min() > 0.2 and t["v0"].max() < 0.5                 # no caustic
+    t2max = t["tau2"].max()
+    # reciprocity holds to the discretisation error (measured at h0 = 1/256:
+    # 3e-10 of max tau^2, 9e-8, 1.5e-3 of max |v1|)
+    assert np.abs(t["tau2"] - t["tau2"].T).max() < 1e-8 * t2max
+    assert np.abs(t["v0"] - t["v0"].T).max() < 1e-6
+    assert np.abs(t["v1"] - t["v1"].T).max() < 1e-2 * v1max
+    # the mirror and diagonal symmetries map the mesh onto itself: to
+    # rounding for tau^2 and v0, to the v1 cycle residual for v1
+    for m in _node_maps():
+        assert np.abs(t["tau2"][np.ix_(m, m)] - t["tau2"]).max() < 1e-12 * t2max
+        assert np.abs(t["v0"][np.ix_(m, m)] - t["v0"]).max() < 1e-10
+        assert np.abs(t["v1"][np.ix_(m, m)] - t["v1"]).max() < 1e-3 * v1max
+    # tau^2 grows with distance as n^2 |r - r0|^2 between the lens's bounds 1 and 1.1
+    xn = chebyshev.nodes(16)
+    px, pz = np.tile(xn, 16), np.repeat(xn, 16)
+    d2 = (px[:, None] - px[None, :]) ** 2 + (pz[:, None] - pz[None, :]) ** 2
+    off = d2 > 0
+    ratio = t["tau2"][off] / d2[off]
+    assert ratio.min() > 1.0 - 1e-9 and ratio.max() < 1.1 ** 2
