@@ -205,6 +205,9 @@ __device__ __forceinline__ void item_mma_n(const uint4* __restrict__ Fs, const u
                                            int lane, float (&acc)[NTW][MT][8]) {
   const uint4* fp = Fs + lane;
   const uint4* xp = Xs + lane;
+  // two k-steps per trip: the second step's fragment loads overlap the
+  // first step's MMAs
+#pragma unroll 2
   for (int k = 0; k < ks; ++k, fp += NTL * 32, xp += MT * 64) {
     uint4 b[NTL];
 #pragma unroll
@@ -218,16 +221,22 @@ __device__ __forceinline__ void item_mma_n(const uint4* __restrict__ Fs, const u
                                __byte_perm(h.z, 0, 0x1032), __byte_perm(h.w, 0, 0x1032)};
       const uint32_t ail[4] = {__byte_perm(l.x, 0, 0x1032), __byte_perm(l.y, 0, 0x1032),
                                __byte_perm(l.z, 0, 0x1032), __byte_perm(l.w, 0, 0x1032)};
+      // each split product over every accumulator before the next: no
+      // two consecutive MMAs of the warp depend on one another
 #pragma unroll
       for (int j = 0; j < NTL; ++j) {
-        float* ar = acc[j][mt];
-        float* ai = acc[j][mt] + 4;
-        mma16816(ar, arh, b[j].x, b[j].y);
-        mma16816(ar, arh, b[j].z, b[j].w);
-        mma16816(ar, arl, b[j].x, b[j].y);
-        mma16816(ai, aih, b[j].x, b[j].y);
-        mma16816(ai, aih, b[j].z, b[j].w);
-        mma16816(ai, ail, b[j].x, b[j].y);
+        mma16816(acc[j][mt], arh, b[j].x, b[j].y);
+        mma16816(acc[j][mt] + 4, aih, b[j].x, b[j].y);
+      }
+#pragma unroll
+      for (int j = 0; j < NTL; ++j) {
+        mma16816(acc[j][mt], arh, b[j].z, b[j].w);
+        mma16816(acc[j][mt] + 4, aih, b[j].z, b[j].w);
+      }
+#pragma unroll
+      for (int j = 0; j < NTL; ++j) {
+        mma16816(acc[j][mt], arl, b[j].x, b[j].y);
+        mma16816(acc[j][mt] + 4, ail, b[j].x, b[j].y);
       }
     }
   }
