@@ -355,6 +355,26 @@ def run_ours(args):
     # apply's output on the sampled rows (same input, deterministic kernels)
     e2e_same = bool(np.array_equal(u_pin[(args.steps - 1) & 1].numpy()[:, rows].T, mixed_rows))
 
+    # ---- the source-inversion step of the 512^2 workload: loss
+    # ||P u(s) - d||^2 over 256 seeded receivers and its gradient through the
+    # adjoint apply (forward + backward, mixed precision)
+    autograd_line = None
+    if w.nrhs == 1 and w.medium.kind == "gradient":
+        from paper_2210_02698_gb300.autograd import hb_apply
+        rng = np.random.default_rng(512)
+        P = torch.from_numpy(np.sort(rng.choice(Nv, 256, replace=False))).to(dev)
+        d_obs = torch.zeros(256, dtype=torch.complex128, device=dev)
+        s_var = s_dev[:1].clone().requires_grad_(True)
+
+        def fwd_bwd():
+            s_var.grad = None
+            loss = (hb_apply(s_var, op)[:, P] - d_obs).abs().pow(2).sum()
+            loss.backward()
+
+        ms_ag = timed(fwd_bwd, args.steps, args.warmup)
+        autograd_line = {"ms_per_step": ms_ag, "what": "loss ||P u(s) - d||^2 over 256 receivers and its "
+                         "gradient (hb_apply forward, hb_apply_adjoint backward), mixed precision"}
+
     result = {}
     if rank == 0:
         hbm, peak_kind = peaks()
@@ -444,6 +464,7 @@ def run_ours(args):
                              "total_device": info["factor_bytes_fp64"] + 2 * info["factor_bytes_mixed"]},
             "max_rank": info["max_rank"],
             "kernel_ms_per_apply": {k: v[0] / nk for k, v in ktimes.items()},
+            **({"autograd": autograd_line} if autograd_line else {}),
             "gather_scatter_ms": gather_ms,
         }
         print(json.dumps(line), flush=True)

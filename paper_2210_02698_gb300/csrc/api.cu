@@ -36,7 +36,7 @@ void free_all(hb_ctx* c) {
   for (void* p : {(void*)c->d_nodes, (void*)c->d_tab, (void*)c->d_LX, (void*)c->d_LZ, (void*)c->d_H[0],
                   (void*)c->d_H[1], (void*)c->d_ncell, (void*)c->d_self, (void*)c->d_perm, (void*)c->d_f64,
                   (void*)c->d_nat[0], (void*)c->d_nat[1], (void*)c->d_pperm, (void*)c->d_mx,
-                  (void*)c->d_mxh, c->d_x, c->d_y})
+                  (void*)c->d_mxh, c->d_x, c->d_y, (void*)c->d_dense_part})
     hb::dev_free(p);
   hb::dev_free(c->d_xh);
   hb::dev_free(c->d_tasks[0]);

@@ -195,15 +195,18 @@ EntryParams entry_params(const hb_ctx* c, int transposed) {
 
 // ------------------------------------------------------- dense apply ----
 // One CTA owns 64 consecutive cells of one grid line (the outputs) and sweeps
-// every source line segment of 64 cells.  Thread t: output o = t & 63,
-// quarter t >> 6 takes every 4th source of the segment.  RC right-hand sides
-// per pass.  FP64 throughout.
+// the source line segments of 64 cells of its share of the source lines
+// (blockIdx.y of gridDim.y contiguous shares; all lines when gridDim.y = 1).
+// Thread t: output o = t & 63, quarter t >> 6 takes every 4th source of the
+// segment.  RC right-hand sides per pass.  FP64 throughout.  With one share
+// the CTA writes u; with several it writes its unscaled partial sums to
+// part[share][r][cell] and dense_reduce_kernel adds the shares in order.
 constexpr int DT = 64;
 
 template <int RC, bool ADJ>
 __global__ void __launch_bounds__(256) dense_kernel(EntryParams p, const double2* __restrict__ s,
                                                     double2* __restrict__ u, long long Nv, int r0,
-                                                    double scale) {
+                                                    double scale, double2* __restrict__ part) {
   extern __shared__ double smem[];
   const int nI = p.nI;
   double* LXo = smem;                         // DT x 16
@@ -230,7 +233,9 @@ __global__ void __launch_bounds__(256) dense_kernel(EntryParams p, const double2
   for (int r = 0; r < RC; ++r) acc[r] = make_double2(0.0, 0.0);
   const int NI = p.NI;
 
-  for (int bq = 0; bq < p.ny; ++bq) {
+  const int bq0 = (int)((long long)p.ny * blockIdx.y / gridDim.y);
+  const int bq1 = (int)((long long)p.ny * (blockIdx.y + 1) / gridDim.y);
+  for (int bq = bq0; bq < bq1; ++bq) {
     __syncthreads();
     // M[q][i1][j1] = sum_i2 LZ[bo][i2] H[q][bq][(i2,i1)][j1]
     for (int idx = t; idx < 3 * nI * nI; idx += blockDim.x) {
@@ -300,34 +305,75 @@ __global__ void __launch_bounds__(256) dense_kernel(EntryParams p, const double2
         a.x += b.x;
         a.y += b.y;
       }
-      u[(size_t)(r0 + r) * Nv + onat] = make_double2(a.x * scale, a.y * scale);
+      if (part) part[((size_t)blockIdx.y * RC + r) * Nv + onat] = a;
+      else u[(size_t)(r0 + r) * Nv + onat] = make_double2(a.x * scale, a.y * scale);
     }
+  }
+}
+
+// u[r0 + r][cell] = scale * (sum over the shares, in order, of part[share][r][cell])
+__global__ void dense_reduce_kernel(const double2* __restrict__ part, double2* __restrict__ u, long long Nv, int rc,
+                                    int nsplit, int r0, double scale) {
+  const long long n = Nv * rc;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double2 a = make_double2(0.0, 0.0);
+    for (int k = 0; k < nsplit; ++k) {
+      const double2 b = part[(size_t)k * n + i];
+      a.x += b.x;
+      a.y += b.y;
+    }
+    const long long r = i / Nv, cell = i - r * Nv;
+    u[(size_t)(r0 + r) * Nv + cell] = make_double2(a.x * scale, a.y * scale);
   }
 }
 
 template <int RC, bool ADJ>
 static void launch_dense(const EntryParams& p, const double2* s, double2* u, long long Nv, int r0,
-                         double scale, cudaStream_t st) {
+                         double scale, int nsplit, double2* part, cudaStream_t st) {
   size_t sm = sizeof(double) * (DT * MAX_NI + 3 * MAX_NI * MAX_NI + 3 * DT * MAX_NI) +
               sizeof(double2) * (DT * RC + 3 * DT * RC);
   auto k = dense_kernel<RC, ADJ>;
   HB_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   int ntx = (p.nx + DT - 1) / DT;
-  k<<<ntx * p.ny, 256, sm, st>>>(p, s, u, Nv, r0, scale);
+  k<<<dim3(ntx * p.ny, nsplit), 256, sm, st>>>(p, s, u, Nv, r0, scale, nsplit > 1 ? part : nullptr);
   HB_CHECK_LAUNCH();
+  if (nsplit > 1) {
+    const long long n = Nv * RC;
+    dense_reduce_kernel<<<(unsigned)std::min<long long>((n + 255) / 256, 152LL * 8), 256, 0, st>>>(
+        part, u, Nv, RC, nsplit, r0, scale);
+    HB_CHECK_LAUNCH();
+  }
 }
 
 void dense_apply(hb_ctx* c, const double2* s, double2* u, int nrhs, int adjoint, cudaStream_t st) {
   EntryParams p = entry_params(c, adjoint);
   const double scale = c->h * c->h;
+  // small grids give few output CTAs: split the source lines into shares so
+  // that there are at least eight CTAs per SM (the entry evaluation is
+  // latency-bound FP64 work)
+  int dev = 0, nsm = 0;
+  HB_CUDA(cudaGetDevice(&dev));
+  HB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const long long cta = (long long)((p.nx + DT - 1) / DT) * p.ny;
+  const int nsplit = (int)std::max<long long>(1, std::min<long long>(p.ny, (8LL * nsm + cta - 1) / cta));
+  if (nsplit > 1) {
+    const size_t need = (size_t)nsplit * 16 * (size_t)c->Nv;
+    if (c->dense_part_cap < need) {
+      dev_free(c->d_dense_part);
+      c->d_dense_part = nullptr;
+      c->dense_part_cap = 0;
+      c->d_dense_part = dev_alloc<double2>(need);
+      c->dense_part_cap = need;
+    }
+  }
   int r0 = 0;
   while (r0 < nrhs) {
     int left = nrhs - r0;
     int rc = left >= 16 ? 16 : left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
 #define HB_DENSE_CASE(R)                                                              \
   case R:                                                                             \
-    if (adjoint) launch_dense<R, true>(p, s, u, c->Nv, r0, scale, st);                \
-    else launch_dense<R, false>(p, s, u, c->Nv, r0, scale, st);                       \
+    if (adjoint) launch_dense<R, true>(p, s, u, c->Nv, r0, scale, nsplit, c->d_dense_part, st); \
+    else launch_dense<R, false>(p, s, u, c->Nv, r0, scale, nsplit, c->d_dense_part, st);       \
     break;
     switch (rc) {
       HB_DENSE_CASE(16)

@@ -214,6 +214,9 @@ struct hb_ctx {
   // mixed apply scratch (native layout, up to 32 right-hand sides)
   uint4* d_mx = nullptr;
   uint4* d_mxh = nullptr;
+  // dense apply: per-split partial sums when source lines are split over CTAs
+  double2* d_dense_part = nullptr;
+  size_t dense_part_cap = 0;
 
   // timing
   bool timing = false;
