@@ -188,7 +188,12 @@ hb_status hb_set_wait_selftest(hb_handle h, int on);
 /* hb_apply_dense / hb_apply_dense_adjoint: the same sums (Eq. m_v2v) and
  * their adjoint, matrix free, every entry evaluated in FP64 on the fly
  * (Eq. chebinterpblock, Eq. babich, Appendix A).  Needs no hb_build.
- * Same layout and limits as hb_apply. */
+ * Same layout and limits as hb_apply.  On grids with fewer than eight
+ * 64-cell output segments per SM the source lines are split over CTAs and
+ * the first such call allocates the per-share partial sums (owned by the
+ * handle, freed by hb_destroy): make that first call outside a CUDA graph
+ * capture.  Results do not depend on the split being taken or not beyond
+ * the order of the FP64 additions. */
 hb_status hb_apply_dense(hb_handle h, const void* s, void* u, int nrhs, void* stream);
 hb_status hb_apply_dense_adjoint(hb_handle h, const void* u, void* s, int nrhs, void* stream);
 
