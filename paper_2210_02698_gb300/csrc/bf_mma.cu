@@ -328,6 +328,7 @@ __global__ void __launch_bounds__(NWARP * 32, 1) bf_step_kernel(StepArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t full[NWARP][MAX_STAGES];
   __shared__ __align__(16) WItem slot[NWARP][MAX_STAGES];
+  __shared__ __align__(16) int4 recs[NWARP][32][2];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nst = a.stages;
   auto buf = [&](int id) { return id == 0 ? a.x : a.xh; };   // inputs come from x or xh
@@ -354,7 +355,8 @@ __global__ void __launch_bounds__(NWARP * 32, 1) bf_step_kernel(StepArgs a) {
 
   // Item records: the warp keeps two windows of 32 in registers (lane j
   // holds record 32 w + j of window w), loading window w + 1 when the first
-  // item of window w is issued; an issued record is broadcast from its lane.
+  // item of window w is issued; at that point window w moves to shared
+  // memory, where lane 0 reads the record of each item it issues.
   int4 w0lo = make_int4(0, 0, 0, 0), w0hi = w0lo, w1lo = w0lo, w1hi = w0lo;
   auto load_win = [&](long long w) {
     const long long q = 32 * w + lane;
@@ -376,19 +378,17 @@ __global__ void __launch_bounds__(NWARP * 32, 1) bf_step_kernel(StepArgs a) {
   // all lanes: stage s gets item q; lane 0 stores its record, arms the
   // barrier and fetches the factor run (and the input run when with_x)
   auto issue = [&](int s, long long q, bool with_x) {
-    if (q >= 32 && (q & 31) == 0) load_win((q >> 5) + 1);
-    const bool odd = (q >> 5) & 1;
-    const int src = (int)(q & 31);
-    int4 lo = odd ? w1lo : w0lo, hi = odd ? w1hi : w0hi;
-    lo.x = __shfl_sync(0xffffffffu, lo.x, src);
-    lo.y = __shfl_sync(0xffffffffu, lo.y, src);
-    lo.z = __shfl_sync(0xffffffffu, lo.z, src);
-    lo.w = __shfl_sync(0xffffffffu, lo.w, src);
-    hi.x = __shfl_sync(0xffffffffu, hi.x, src);
-    hi.y = __shfl_sync(0xffffffffu, hi.y, src);
-    hi.z = __shfl_sync(0xffffffffu, hi.z, src);
-    hi.w = __shfl_sync(0xffffffffu, hi.w, src);
+    if ((q & 31) == 0) {
+      // the window of item q goes to shared memory (its loads were issued 32
+      // items ago), then the next window is fetched into the freed registers
+      const bool odd = (q >> 5) & 1;
+      recs[warp][lane][0] = odd ? w1lo : w0lo;
+      recs[warp][lane][1] = odd ? w1hi : w0hi;
+      __syncwarp();
+      if (q >= 32) load_win((q >> 5) + 1);
+    }
     if (lane == 0) {
+      const int4 lo = recs[warp][q & 31][0], hi = recs[warp][q & 31][1];
       int4* d = reinterpret_cast<int4*>(&sl[s]);
       d[0] = lo;
       d[1] = hi;
@@ -596,10 +596,11 @@ struct FlowPlan {
 
 // k-steps per item for groups of ntl n-tiles: at one m-tile, ITEM_BYTES
 // bounds the factor run plus the input run counted at two m-tiles (so an
-// item is at most 12 KB); at two m-tiles the bound is 14 KB (8 warps x 2
-// stages fit in 227 KB).
+// item is at most 12 KB); at two m-tiles the bound is 13 KB (an item is then
+// at most 12.5 KB, and 8 warps x 2 stages fit in 227 KB beside the record
+// windows).
 static int item_ks(int ntl, int MT) {
-  return std::max(1, (MT == 1 ? ITEM_BYTES : 14336) / (512 * ntl + 2048));
+  return std::max(1, (MT == 1 ? ITEM_BYTES : 13312) / (512 * ntl + 2048));
 }
 
 // The chains of one task for MT m-tiles: group g holds n-tiles
