@@ -20,6 +20,8 @@ Modules (each function cites the passage it follows):
   the transport equations (Sec. 2.3, Eq. faceik, Eq. equVs) on a mesh, for
   media without closed-form ingredients (the Gaussian lens); numerics in
   plain C (``sweep.c``, compiled with gcc on first use).
+* ``rays``      - ray tracing of the eikonal and the ray-tube form of the v0
+  transport equation (Sec. 2): a mesh-free cross-check of ``sweep``.
 * ``hankel``    - the Hankel-type functions f_q (Eq. termf).
 * ``kernel``    - matrix entries g = v0 f0 + v1 f1 (Eq. babich) and the 2D
   self term (Appendix A, Eq. HankelIntegral2dlemma).
