@@ -407,6 +407,16 @@ def run_ours(args):
                              f"({dt:.1f} s)",
                    "rel_l2_mixed_vs_oracle": float(np.linalg.norm(got - U_ref) / np.linalg.norm(U_ref)),
                    "rel_l2_fp64_vs_oracle": float(np.linalg.norm(got64 - U_ref) / np.linalg.norm(U_ref))}
+            if w.rhs_kind == "mixed64":
+                # the four source kinds (quarters of the columns) on their own:
+                # smooth bumps and wavepackets radiate little at this frequency
+                q = R // 4
+                kinds = ("point", "line", "gaussian_bump", "wavepacket")
+                cpu["rel_l2_mixed_by_source_kind"] = {
+                    kinds[k]: float(np.linalg.norm(got[:, k * q:(k + 1) * q] - U_ref[:, k * q:(k + 1) * q]) /
+                                    np.linalg.norm(U_ref[:, k * q:(k + 1) * q])) for k in range(4)}
+                cpu["output_norm_by_source_kind"] = {
+                    kinds[k]: float(np.linalg.norm(U_ref[:, k * q:(k + 1) * q])) for k in range(4)}
         except Exception as ex:  # the baseline must never break the bench line
             cpu = {"value": None, "unit": UNIT, "cores": nc, "kind": "oracle", "sample": f"failed: {ex}"}
         # the oracle's CPU butterfly apply over the saved factors (all rows, all RHS)
