@@ -185,6 +185,17 @@ hb_status hb_set_precision(hb_handle h, int precision);
  * Errors: HB_ERR_ARG for a null handle. */
 hb_status hb_set_wait_selftest(hb_handle h, int on);
 
+/* hb_device_alloc_cap: test hook for the out-of-memory paths.  Every device
+ * allocation of the library is counted; with cap_bytes > 0 an allocation
+ * that would take the live total above cap_bytes fails as a real
+ * out-of-memory does (HB_ERR_OOM from the call that needed it); 0 removes
+ * the cap, a negative value leaves it unchanged.  *live_bytes (if not NULL)
+ * receives the bytes the library holds now.  Process-wide, not tied to a
+ * handle; no device work.  A build that fails for lack of memory frees what
+ * it allocated and leaves the handle unbuilt (hb_build may be called
+ * again); an apply that fails for lack of scratch may be repeated. */
+hb_status hb_device_alloc_cap(long long cap_bytes, long long* live_bytes);
+
 /* hb_apply_dense / hb_apply_dense_adjoint: the same sums (Eq. m_v2v) and
  * their adjoint, matrix free, every entry evaluated in FP64 on the fly
  * (Eq. chebinterpblock, Eq. babich, Appendix A).  Needs no hb_build.

@@ -22,7 +22,7 @@ STATUS = {0: "HB_OK", 1: "HB_ERR_ARG", 2: "HB_ERR_CUDA", 3: "HB_ERR_OOM", 4: "HB
 
 # every symbol include/hb.h declares
 EXPORTS = ["hb_create", "hb_build", "hb_save", "hb_load", "hb_apply", "hb_apply_adjoint", "hb_set_precision",
-           "hb_set_wait_selftest",
+           "hb_set_wait_selftest", "hb_device_alloc_cap",
            "hb_apply_dense", "hb_apply_dense_adjoint", "hb_entries", "hb_id_batch", "hb_id_batch_noalloc",
            "hb_tree_perm", "hb_proxy_rows", "hb_info", "hb_set_kernel_timing",
            "hb_kernel_times", "hb_last_error", "hb_destroy"]
@@ -72,6 +72,7 @@ def lib():
         L.hb_save.argtypes = [vp, C.c_char_p]
         L.hb_load.argtypes = [C.c_char_p, vp]
         L.hb_set_wait_selftest.argtypes = [vp, i]
+        L.hb_device_alloc_cap.argtypes = [ll, C.POINTER(ll)]
         L.hb_entries.argtypes = [vp, vp, i, vp, i, vp, vp]
         L.hb_id_batch.argtypes = [i, vp, vp, vp, vp, d, vp, vp, vp]
         L.hb_id_batch_noalloc.argtypes = [i, vp, vp, vp, vp, d, vp, vp, vp, vp]
@@ -89,6 +90,14 @@ def lib():
                 getattr(L, f).restype = C.c_int
         _LIB = L
     return _LIB
+
+
+def device_alloc_cap(cap_bytes=-1):
+    """hb_device_alloc_cap: set the cap on the library's live device bytes
+    (0: none, negative: unchanged) and return the bytes held now."""
+    live = C.c_longlong(0)
+    _check(lib().hb_device_alloc_cap(int(cap_bytes), C.byref(live)))
+    return live.value
 
 
 class HBError(RuntimeError):

@@ -3,13 +3,89 @@
 // kernels of entries.cu, cpqr.cu, build.cu and apply.cu.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "hb_internal.cuh"
+
+// ------------------------------------------------- allocation registry ----
+namespace {
+struct Registry {
+  std::mutex m;
+  std::unordered_map<void*, size_t> bytes;
+  long long live = 0;
+  long long cap = 0;   // 0: no cap
+};
+Registry& registry() {
+  static Registry* r = new Registry();   // never destroyed: frees may come late
+  return *r;
+}
+thread_local std::vector<void*>* g_build_allocs = nullptr;
+}  // namespace
+
+namespace hb {
+
+void* registry_alloc(size_t bytes) {
+  Registry& r = registry();
+  {
+    std::lock_guard<std::mutex> lock(r.m);
+    if (r.cap > 0 && r.live + (long long)bytes > r.cap)
+      throw Error{HB_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes exceeds the cap of " +
+                                  std::to_string(r.cap) + " bytes (hb_device_alloc_cap)"};
+  }
+  void* p = nullptr;
+  const cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw Error{e == cudaErrorMemoryAllocation ? HB_ERR_OOM : HB_ERR_CUDA,
+                "cudaMalloc(" + std::to_string(bytes) + " bytes): " + cudaGetErrorString(e)};
+  }
+  {
+    std::lock_guard<std::mutex> lock(r.m);
+    r.bytes[p] = bytes;
+    r.live += (long long)bytes;
+  }
+  if (g_build_allocs) g_build_allocs->push_back(p);
+  return p;
+}
+
+void registry_free(void* p) {
+  Registry& r = registry();
+  {
+    std::lock_guard<std::mutex> lock(r.m);
+    auto it = r.bytes.find(p);
+    if (it != r.bytes.end()) {
+      r.live -= (long long)it->second;
+      r.bytes.erase(it);
+    }
+  }
+  if (g_build_allocs) {
+    auto it = std::find(g_build_allocs->begin(), g_build_allocs->end(), p);
+    if (it != g_build_allocs->end()) g_build_allocs->erase(it);
+  }
+  cudaFree(p);
+}
+
+BuildAllocs::BuildAllocs() { g_build_allocs = new std::vector<void*>(); }
+
+BuildAllocs::~BuildAllocs() {
+  delete g_build_allocs;
+  g_build_allocs = nullptr;
+}
+
+void BuildAllocs::free_all() {
+  std::vector<void*> v;
+  v.swap(*g_build_allocs);
+  for (void* p : v) registry_free(p);
+}
+
+}  // namespace hb
 
 namespace {
 
@@ -151,8 +227,34 @@ hb_status hb_build(hb_handle h) {
   return guarded(h, [&] {
     if (!h) throw hb::arg_error("null handle");
     if (h->built) throw hb::Error{HB_ERR_STATE, "already built"};
-    hb::build(h);
+    hb::BuildAllocs allocs;
+    try {
+      hb::build(h);
+    } catch (...) {
+      // a failed build frees what it allocated and leaves the handle unbuilt
+      cudaDeviceSynchronize();
+      cudaGetLastError();
+      allocs.free_all();
+      h->d_f64 = nullptr;
+      h->d_tasks[0] = h->d_tasks[1] = nullptr;
+      h->d_nat[0] = h->d_nat[1] = nullptr;
+      h->d_pperm = nullptr;
+      for (int d = 0; d < 2; ++d) {
+        hb::flow_plan_free(h->flow_plan[d]);
+        h->flow_plan[d] = nullptr;
+      }
+      throw;
+    }
     h->built = true;
+  });
+}
+
+hb_status hb_device_alloc_cap(long long cap_bytes, long long* live_bytes) {
+  return guarded(nullptr, [&] {
+    Registry& r = registry();
+    std::lock_guard<std::mutex> lock(r.m);
+    if (cap_bytes >= 0) r.cap = cap_bytes;
+    if (live_bytes) *live_bytes = r.live;
   });
 }
 

@@ -176,9 +176,13 @@ void ensure_scratch(hb_ctx* c, int nrhs, bool fp64) {
     fresh = true;
     c->d_perm = upload(c->perm);
   }
-  if (!fp64 && !c->d_mx) {
-    // native vectors for two m-tiles: 2 KB per row tile
+  if (!fp64 && (!c->d_mx || !c->d_mxh)) {
+    // native vectors for two m-tiles: 2 KB per row tile (both or neither:
+    // an allocation that failed half way is redone whole on the next call)
     fresh = true;
+    dev_free(c->d_mx);
+    dev_free(c->d_mxh);
+    c->d_mx = c->d_mxh = nullptr;
     c->d_mx = dev_alloc<uint4>((size_t)std::max<long long>(c->nv_tiles, 1) * 128);
     c->d_mxh = dev_alloc<uint4>((size_t)std::max<long long>(c->xh_tiles, 1) * 128);
   }

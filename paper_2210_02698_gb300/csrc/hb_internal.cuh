@@ -40,23 +40,34 @@ inline Error arg_error(const char* fmt, ...) {
   return Error{HB_ERR_ARG, buf};
 }
 
+// Every device allocation of the library goes through the registry
+// (api.cu): it counts the live bytes, applies the optional cap of
+// hb_device_alloc_cap (a cap that would be exceeded fails like a real
+// out-of-memory, HB_ERR_OOM), and records the allocations made while a
+// BuildAllocs scope is open on the calling thread.
+void* registry_alloc(size_t bytes);   // throws Error (HB_ERR_OOM / HB_ERR_CUDA)
+void registry_free(void* p);
+
+// The allocations made by one hb_build: on failure free_all() releases
+// those still live, so that a failed build leaves nothing behind.
+class BuildAllocs {
+ public:
+  BuildAllocs();
+  ~BuildAllocs();
+  void free_all();
+  BuildAllocs(const BuildAllocs&) = delete;
+  BuildAllocs& operator=(const BuildAllocs&) = delete;
+};
+
 // Device allocation that reports HB_ERR_OOM.
 template <class T>
 T* dev_alloc(size_t count) {
   if (count == 0) count = 1;
-  void* p = nullptr;
-  cudaError_t e = cudaMalloc(&p, count * sizeof(T));
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    throw Error{e == cudaErrorMemoryAllocation ? HB_ERR_OOM : HB_ERR_CUDA,
-                std::string("cudaMalloc(") + std::to_string(count * sizeof(T)) +
-                    " bytes): " + cudaGetErrorString(e)};
-  }
-  return static_cast<T*>(p);
+  return static_cast<T*>(registry_alloc(count * sizeof(T)));
 }
 
 inline void dev_free(void* p) {
-  if (p) cudaFree(p);
+  if (p) registry_free(p);
 }
 
 template <class T>

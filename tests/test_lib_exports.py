@@ -64,3 +64,16 @@ def test_no_device_is_an_error_not_a_fallback(L):
     o = binding.Options(1e-6, 4, 20.0, 10.0, 0, 0, 0)
     hnd = C.c_void_p()
     assert L.hb_create(C.byref(g), C.byref(t), 5.0, C.byref(o), C.byref(hnd)) == binding.HB_ERR_CUDA
+
+
+def test_device_alloc_cap_is_host_state(L):
+    """hb_device_alloc_cap only sets a number and reports the library's live
+    device bytes (none before any handle exists): no device work."""
+    from paper_2210_02698_gb300 import binding
+    live = binding.device_alloc_cap(-1)
+    assert live >= 0
+    try:
+        assert binding.device_alloc_cap(1 << 20) == live
+        assert binding.device_alloc_cap(-1) == live
+    finally:
+        binding.device_alloc_cap(0)
