@@ -228,6 +228,7 @@ hb_status hb_build(hb_handle h) {
     if (!h) throw hb::arg_error("null handle");
     if (h->built) throw hb::Error{HB_ERR_STATE, "already built"};
     hb::BuildAllocs allocs;
+    hb::NvtxRange nr("hb_build");
     try {
       hb::build(h);
     } catch (...) {

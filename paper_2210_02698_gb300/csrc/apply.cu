@@ -130,6 +130,7 @@ struct TimerScope {
     return (int)c->tnames.size() - 1;
   }
   void begin(const char* name) {
+    nvtxRangePushA(name);   // host-side phase marker (matched in end())
     if (!c->timing) return;
     cudaEvent_t a, b;
     HB_CUDA(cudaEventCreate(&a));
@@ -138,6 +139,7 @@ struct TimerScope {
     ev.push_back({group(name), {a, b}});
   }
   void end() {
+    nvtxRangePop();
     if (!c->timing) return;
     HB_CUDA(cudaEventRecord(ev.back().second.second, st));
   }
@@ -211,6 +213,7 @@ void run_steps(hb_ctx* c, const C* F, int nrhs, int dir, cudaStream_t st, TimerS
 }  // namespace
 
 void apply_bf(hb_ctx* c, const double2* s, double2* u, int nrhs, int adjoint, int precision, cudaStream_t st) {
+  NvtxRange nr(adjoint ? "hb_apply_adjoint" : "hb_apply");
   if (c->h_err && *reinterpret_cast<volatile int*>(c->h_err)) {
     *reinterpret_cast<volatile int*>(c->h_err) = 0;
     throw Error{HB_ERR_TIMEOUT, "a bounded device wait of an earlier apply gave up"};

@@ -346,6 +346,7 @@ static void launch_dense(const EntryParams& p, const double2* s, double2* u, lon
 }
 
 void dense_apply(hb_ctx* c, const double2* s, double2* u, int nrhs, int adjoint, cudaStream_t st) {
+  NvtxRange nr(adjoint ? "hb_apply_dense_adjoint" : "hb_apply_dense");
   EntryParams p = entry_params(c, adjoint);
   const double scale = c->h * c->h;
   // small grids give few output CTAs: split the source lines into shares so

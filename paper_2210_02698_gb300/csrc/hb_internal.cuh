@@ -2,6 +2,7 @@
 // translation units (not part of the C ABI).
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstdarg>
 #include <cstdint>
@@ -39,6 +40,15 @@ inline Error arg_error(const char* fmt, ...) {
   va_end(ap);
   return Error{HB_ERR_ARG, buf};
 }
+
+// A named NVTX range for the scope (build stages, apply phases; no-ops
+// unless a profiler is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Every device allocation of the library goes through the registry
 // (api.cu): it counts the live bytes, applies the optional cap of
