@@ -144,3 +144,28 @@ def test_autograd_gradient_matches_finite_differences():
                 fd = (loss(s0 + t * dl) - loss(s0 - t * dl)) / (2 * t)
             pred = torch.real(torch.vdot(g.reshape(-1), dl.reshape(-1)))
             assert abs(float(fd - pred)) <= tol * abs(float(pred)) + tol * float(g.norm() * dl.norm())
+
+
+def test_maximum_rhs_on_a_small_grid():
+    """1024 right-hand sides (the documented maximum; 32 mixed passes, 64 FP64
+    passes) on a 16 x 16 grid with two tree levels; 1025 is refused."""
+    import torch
+    from oracle import dense
+    from paper_2210_02698_gb300 import binding
+    w = W.small_workload(W.GRADIENT, 16, 2, 1024)
+    og, gp = oracle_op(w), gpu_op(w, precision=binding.HB_FP64)
+    gp.build()
+    s = W.complex_normal_sources(w.grid.Nv, 1024, 77)
+    want = dense.apply(og, s)
+    assert rel_l2(_apply(gp, s), want) < 1e-5
+    gp.set_precision(binding.HB_MIXED_BF16X3)
+    got = _apply(gp, s)
+    assert rel_l2(got, want) < 1e-4
+    assert np.max(np.linalg.norm(got - want, axis=0) / np.linalg.norm(want, axis=0)) < 1e-4
+    wantA = dense.adjoint(og, s)
+    assert rel_l2(_apply(gp, s, adjoint=True), wantA) < 1e-4
+    s1 = torch.zeros((1025, w.grid.Nv), dtype=torch.complex128, device="cuda")
+    with pytest.raises(binding.HBError) as e:
+        gp.apply(s1, torch.empty_like(s1), 1025)
+    assert e.value.status == binding.HB_ERR_ARG
+    gp.close()
