@@ -46,9 +46,10 @@ def test_tree_and_proxy_rows_match_oracle(N, leaf):
         assert np.array_equal(gp.proxy_rows(t0, t1, seeds), want)
 
 
-# 24 RHS: one pass of two m-tiles; 40 RHS: passes of 32 (two m-tiles) + 8 (one); 17: FP64 passes 16 + 1
+# 24 RHS: one pass of two m-tiles; 40 RHS: passes of 32 (two m-tiles) + 8 (one); 17: FP64 passes 16 + 1;
+# 8 x 8: a single leaf (no butterfly at all); 9 x 9: two leaves of 41 and 40 cells
 @pytest.mark.parametrize("N,leaf,nrhs", [(32, 64, 3), (48, 32, 2), (64, 64, 4), (48, 64, 24), (32, 32, 40),
-                                         (40, 64, 17)])
+                                         (40, 64, 17), (8, 64, 2), (9, 64, 3)])
 def test_butterfly_fp64_and_mixed_vs_dense_oracle(N, leaf, nrhs):
     from oracle import dense
     from paper_2210_02698_gb300 import binding
