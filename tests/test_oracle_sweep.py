@@ -161,3 +161,15 @@ def test_lens_tables_match_ray_tracing():
         assert res.max() < 1e-12
         assert np.abs(T * T - t["tau2"][obs, j]).max() < 2e-9
         assert np.abs(v0 - t["v0"][obs, j]).max() < 3e-7
+
+
+def test_stored_lens_tables_are_the_builders_output():
+    """Provenance of the stored lens tables: one column regenerated by the
+    committed builder at the stored mesh (h0 = 1/256) reproduces them (to
+    rounding: contraction of multiply-adds may differ between compilers)."""
+    t, _ = _lens()
+    j = 137
+    r = sweep.build_tables(W.LENS, 16, h0=1 / 256, sources=[j])
+    assert np.abs(r["tau2"][:, 0] - t["tau2"][:, j]).max() < 1e-12 * t["tau2"].max()
+    assert np.abs(r["v0"][:, 0] - t["v0"][:, j]).max() < 1e-10
+    assert np.abs(r["v1"][:, 0] - t["v1"][:, j]).max() < 1e-8
