@@ -173,3 +173,28 @@ def test_stored_lens_tables_are_the_builders_output():
     assert np.abs(r["tau2"][:, 0] - t["tau2"][:, j]).max() < 1e-12 * t["tau2"].max()
     assert np.abs(r["v0"][:, 0] - t["v0"][:, j]).max() < 1e-10
     assert np.abs(r["v1"][:, 0] - t["v1"][:, j]).max() < 1e-8
+
+
+def test_ray_v1_reproduces_gradient_closed_form():
+    """v1 by the ray form of Eq. equVs (s = 0) with Lap v0 from ray-traced v0
+    against the gradient medium's v1 (the oracle's quadrature of the same
+    equation in closed-form coefficients)."""
+    xn = chebyshev.nodes(16)
+    px, pz = np.tile(xn, 16), np.repeat(xn, 16)
+    med = W.GRADIENT
+    for j, obs in _sample_pairs(5, nsrc=3, nobs=5):
+        v1 = rays.v1_along_ray(med, px[j], pz[j], px[obs], pz[obs])
+        et = tables.tau_gradient(px[obs], pz[obs], px[j], pz[j], med.c0, med.g)
+        assert np.abs(v1 - tables.v1_gradient(et, med.g)).max() < 1e-6
+
+
+def test_lens_v1_matches_ray_transport():
+    """The lens tables' v1 (first-order accurate by construction: two
+    differences of v0) against the ray form of the transport equation
+    (measured: within 6.2e-5 on 64 pairs, |v1| up to 0.19)."""
+    t, _ = _lens()
+    xn = chebyshev.nodes(16)
+    px, pz = np.tile(xn, 16), np.repeat(xn, 16)
+    for j, obs in _sample_pairs(11, nsrc=4, nobs=6):
+        v1 = rays.v1_along_ray(W.LENS, px[j], pz[j], px[obs], pz[obs])
+        assert np.abs(v1 - t["v1"][obs, j]).max() < 2e-4
