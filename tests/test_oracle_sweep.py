@@ -198,3 +198,23 @@ def test_lens_v1_matches_ray_transport():
     for j, obs in _sample_pairs(11, nsrc=4, nobs=6):
         v1 = rays.v1_along_ray(W.LENS, px[j], pz[j], px[obs], pz[obs])
         assert np.abs(v1 - t["v1"][obs, j]).max() < 2e-4
+
+
+def test_lens_rays_do_not_cross():
+    """No caustic in the lens (the method assumes a single-valued tau): over
+    fans of 360 rays from corner, centre and interior sources, the ray-tube
+    width J (positive orientation of the fan) stays far from zero wherever
+    the rays are inside the unit square (measured: J >= 0.61 tau)."""
+    th = np.linspace(0, 2 * np.pi, 361)[:-1]
+    dth = 1e-4
+    for x0, z0 in [(0.0024, 0.0024), (0.5, 0.5), (0.2, 0.7)]:
+        for T in np.linspace(0.05, 1.6, 8):
+            TT = np.full_like(th, T)
+            y = rays.trace(W.LENS, x0, z0, th, TT, 200)
+            yp = rays.trace(W.LENS, x0, z0, th + dth, TT, 200)
+            ym = rays.trace(W.LENS, x0, z0, th - dth, TT, 200)
+            jx, jz = (yp[0] - ym[0]) / (2 * dth), (yp[1] - ym[1]) / (2 * dth)
+            width = -(jx * y[3] - jz * y[2]) / np.hypot(y[2], y[3])
+            ins = (y[0] >= 0) & (y[0] <= 1) & (y[1] >= 0) & (y[1] <= 1)
+            if ins.any():
+                assert (width[ins] / T).min() > 0.3
