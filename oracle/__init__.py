@@ -22,6 +22,9 @@ Modules (each function cites the passage it follows):
   plain C (``sweep.c``, compiled with gcc on first use).
 * ``rays``      - ray tracing of the eikonal and the ray-tube form of the v0
   transport equation (Sec. 2): a mesh-free cross-check of ``sweep``.
+* ``inclusion`` - scattering by a curve inclusion (Sec. 3.2): K^{s2s},
+  K^{v2s}, K^{s2v} and the total field of Eq. m_v2v_inclu, with the exact
+  circle series that pins them.
 * ``hankel``    - the Hankel-type functions f_q (Eq. termf).
 * ``kernel``    - matrix entries g = v0 f0 + v1 f1 (Eq. babich) and the 2D
   self term (Appendix A, Eq. HankelIntegral2dlemma).
