@@ -166,15 +166,23 @@ void setup_tables(hb_ctx* c) {
     HB_CHECK_LAUNCH();
   }
   c->d_ncell = upload(c->n_cells);
+  c->d_self = dev_alloc<double2>(c->Nv);
   std::vector<double> glx, glw;
   gauss_legendre(64, glx, glw);
+  // the quadrature rule is scratch: freed on the way out, also when a step throws
   double* d_gl = upload(glx);
-  double* d_gw = upload(glw);
-  c->d_self = dev_alloc<double2>(c->Nv);
-  self_kernel<<<(unsigned)((c->Nv + 127) / 128), 128>>>(c->d_ncell, c->Nv, c->h, c->omega, d_gl, d_gw,
-                                                        64, c->d_self);
-  HB_CHECK_LAUNCH();
-  HB_CUDA(cudaDeviceSynchronize());
+  double* d_gw = nullptr;
+  try {
+    d_gw = upload(glw);
+    self_kernel<<<(unsigned)((c->Nv + 127) / 128), 128>>>(c->d_ncell, c->Nv, c->h, c->omega, d_gl, d_gw,
+                                                          64, c->d_self);
+    HB_CHECK_LAUNCH();
+    HB_CUDA(cudaDeviceSynchronize());
+  } catch (...) {
+    dev_free(d_gl);
+    dev_free(d_gw);
+    throw;
+  }
   dev_free(d_gl);
   dev_free(d_gw);
 }
@@ -488,14 +496,33 @@ void add_block(BlockBatchHost& B, const hb_ctx* c, const long long* rows, long l
   B.meta.push_back(bm);
 }
 
+namespace {
+// Device scratch of one call, freed when the call returns or throws (after
+// the stream has drained, so no launched kernel still reads it).
+struct CallScratch {
+  cudaStream_t st;
+  std::vector<void*> p;
+  template <class T>
+  T* keep(T* q) {
+    p.push_back(q);
+    return q;
+  }
+  ~CallScratch() {
+    cudaStreamSynchronize(st);
+    for (void* q : p) dev_free(q);
+  }
+};
+}  // namespace
+
 void run_blocks(hb_ctx* c, BlockBatchHost& B, double2* d_out, cudaStream_t st) {
   if (B.items.empty()) return;
-  BlockMeta* d_meta = upload(B.meta, st);
-  long long* d_items = upload(B.items, st);
-  long long* d_rows = upload(B.rows, st);
-  int* d_rdst = upload(B.rdst, st);
-  long long* d_cols = upload(B.cols, st);
-  long long* d_segs = upload(B.segs, st);
+  CallScratch sc{st, {}};
+  BlockMeta* d_meta = sc.keep(upload(B.meta, st));
+  long long* d_items = sc.keep(upload(B.items, st));
+  long long* d_rows = sc.keep(upload(B.rows, st));
+  int* d_rdst = sc.keep(upload(B.rdst, st));
+  long long* d_cols = sc.keep(upload(B.cols, st));
+  long long* d_segs = sc.keep(upload(B.segs, st));
   EntryParams p = entry_params(c, 0);
   size_t nitems = B.items.size();
   for (size_t i0 = 0; i0 < nitems; i0 += 1u << 30) {
@@ -504,12 +531,6 @@ void run_blocks(hb_ctx* c, BlockBatchHost& B, double2* d_out, cudaStream_t st) {
     HB_CHECK_LAUNCH();
   }
   HB_CUDA(cudaStreamSynchronize(st));
-  dev_free(d_meta);
-  dev_free(d_items);
-  dev_free(d_rows);
-  dev_free(d_rdst);
-  dev_free(d_cols);
-  dev_free(d_segs);
 }
 
 void eval_entries(hb_ctx* c, const long long* rows, int m, const long long* cols, int n, double2* out,

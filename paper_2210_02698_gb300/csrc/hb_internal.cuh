@@ -83,7 +83,13 @@ inline void dev_free(void* p) {
 template <class T>
 T* upload(const std::vector<T>& v, cudaStream_t st = 0) {
   T* d = dev_alloc<T>(v.size());
-  if (!v.empty()) HB_CUDA(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+  if (!v.empty()) {
+    const cudaError_t e = cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) {
+      dev_free(d);
+      throw Error{HB_ERR_CUDA, std::string("upload cudaMemcpyAsync: ") + cudaGetErrorString(e)};
+    }
+  }
   return d;
 }
 
