@@ -119,8 +119,8 @@ typedef struct {
  * tables; precompute the Lagrange interpolants at the cell coordinates and
  * the self terms K_ii (Appendix A).  Synchronous.  On success *out owns
  * device memory until hb_destroy.  Errors: HB_ERR_ARG for invalid input
- * (non-positive sizes, n_I < 2 or > 32, omega <= 0, eps <= 0, leaf < 1),
- * HB_ERR_OOM, HB_ERR_CUDA. */
+ * (non-positive sizes, n_I < 2, omega <= 0, eps <= 0, leaf < 1),
+ * HB_ERR_UNSUPPORTED for n_I > 16, HB_ERR_OOM, HB_ERR_CUDA. */
 hb_status hb_create(const hb_grid* grid, const hb_tables* tables, double omega,
                     const hb_options* opts, hb_handle* out);
 
@@ -215,6 +215,44 @@ hb_status hb_apply_dense_adjoint(hb_handle h, const void* u, void* s, int nrhs, 
  * m, n < 1 or an index outside [0, N_v). */
 hb_status hb_entries(hb_handle h, const long long* rows, int m, const long long* cols,
                      int n, void* out, void* stream);
+
+/* Scattering by a curve inclusion (Sec. 3.2).  The curve is given as ns
+ * straight segments: centers (ns x 2, row-major (x, z) pairs), lengths w_i
+ * and the refractive index n_i at each centre, all HOST arrays.  With
+ * g = v0 f0 + v1 f1 interpolated at the points from the handle's tables:
+ *   K^{s2s}_ij = -g(r^s_i, r^s_j) w_j for i != j (Eq. s2s), and on the
+ *     diagonal -(i w_i/4)(1 + (2i/pi)(ln(gamma omega n_i w_i / 4) - 1)),
+ *     gamma = e^{Euler's constant}: minus the integral of (i/4) H0(omega n_i |t|)
+ *     over the segment in its small-argument form;
+ *   K^{v2s}_ij = g(r^s_i, r_j) (Eq. m_v2s),  K^{s2v}_ij = g(r_i, r^s_j) w_j
+ *     (Eq. m_s2v), r_j the cell centres.
+ * The total field vanishes on the curve (Eq. sie; Eq. m_sie: K^{s2s} P = U^inc).
+ *
+ * hb_curve_set: evaluates the three operators densely on the device and
+ * factors K^{s2s} (LU with partial pivoting); replaces an earlier curve.
+ * Synchronous.  Device memory: (2 ns N_v + ns^2) x 16 bytes plus ns x nrhs x
+ * 16 bytes at the first hb_apply_inclusion, owned by the handle until the
+ * next hb_curve_set or hb_destroy.  Errors: HB_ERR_ARG for ns outside
+ * [1, 16384], a non-finite centre, a length or n that is not positive, or a
+ * singular K^{s2s} (the handle then has no curve); HB_ERR_OOM. */
+hb_status hb_curve_set(hb_handle h, const double* centers, const double* lengths, const double* n_seg,
+                       long long ns);
+
+/* hb_curve_operators: K^{s2s} (ns x ns), K^{v2s} (ns x N_v) and K^{s2v}
+ * (N_v x ns) of the curve, evaluated again into caller-owned DEVICE
+ * complex128 column-major buffers (any of them NULL to skip it).
+ * Asynchronous on `stream`.  Errors: HB_ERR_STATE without a curve. */
+hb_status hb_curve_operators(hb_handle h, void* k_s2s, void* k_v2s, void* k_s2v, void* stream);
+
+/* hb_apply_inclusion: the total field with the inclusion (Eq. m_v2v_inclu),
+ *   u = (K^{v2v} + K^{s2v} (K^{s2s})^{-1} K^{v2s}) (h^2 s),
+ * s, u as for hb_apply.  K^{v2v} is applied matrix free in FP64 when
+ * v2v_dense != 0 (no hb_build needed), else by the compressed operator in
+ * the handle's precision (needs hb_build); the surface part runs in FP64.
+ * The first call with more right-hand sides than before allocates the
+ * surface vectors: make it outside a CUDA graph capture.  Errors:
+ * HB_ERR_STATE without a curve, or v2v_dense == 0 before hb_build. */
+hb_status hb_apply_inclusion(hb_handle h, const void* s, void* u, int nrhs, int v2v_dense, void* stream);
 
 /* hb_id_batch: batched column-pivoted QR interpolative decompositions
  * (Eq. ID) of `count` complex128 matrices, with the same rules as the build:

@@ -23,7 +23,8 @@ STATUS = {0: "HB_OK", 1: "HB_ERR_ARG", 2: "HB_ERR_CUDA", 3: "HB_ERR_OOM", 4: "HB
 # every symbol include/hb.h declares
 EXPORTS = ["hb_create", "hb_build", "hb_save", "hb_load", "hb_apply", "hb_apply_adjoint", "hb_set_precision",
            "hb_set_wait_selftest", "hb_device_alloc_cap",
-           "hb_apply_dense", "hb_apply_dense_adjoint", "hb_entries", "hb_id_batch", "hb_id_batch_noalloc",
+           "hb_apply_dense", "hb_apply_dense_adjoint", "hb_entries", "hb_curve_set", "hb_curve_operators",
+           "hb_apply_inclusion", "hb_id_batch", "hb_id_batch_noalloc",
            "hb_tree_perm", "hb_proxy_rows", "hb_info", "hb_set_kernel_timing",
            "hb_kernel_times", "hb_last_error", "hb_destroy"]
 
@@ -74,6 +75,9 @@ def lib():
         L.hb_set_wait_selftest.argtypes = [vp, i]
         L.hb_device_alloc_cap.argtypes = [ll, C.POINTER(ll)]
         L.hb_entries.argtypes = [vp, vp, i, vp, i, vp, vp]
+        L.hb_curve_set.argtypes = [vp, vp, vp, vp, ll]
+        L.hb_curve_operators.argtypes = [vp, vp, vp, vp, vp]
+        L.hb_apply_inclusion.argtypes = [vp, vp, vp, i, i, vp]
         L.hb_id_batch.argtypes = [i, vp, vp, vp, vp, d, vp, vp, vp]
         L.hb_id_batch_noalloc.argtypes = [i, vp, vp, vp, vp, d, vp, vp, vp, vp]
         L.hb_tree_perm.argtypes = [vp, vp]
@@ -205,6 +209,27 @@ class Operator:
         rows = np.ascontiguousarray(rows, dtype=np.int64)
         cols = np.ascontiguousarray(cols, dtype=np.int64)
         self._call("hb_entries", rows.ctypes.data, len(rows), cols.ctypes.data, len(cols), _ptr(out),
+                   _stream_ptr(stream))
+
+    def set_curve(self, centers, lengths, n_seg):
+        """hb_curve_set: the inclusion's segments (centres (ns, 2), lengths,
+        n at the centres; host arrays)."""
+        c = np.ascontiguousarray(centers, dtype=np.float64).reshape(-1, 2)
+        w = np.ascontiguousarray(lengths, dtype=np.float64)
+        n = np.ascontiguousarray(n_seg, dtype=np.float64)
+        if not (len(c) == len(w) == len(n)):
+            raise ValueError("centers, lengths and n_seg differ in length")
+        self._call("hb_curve_set", c.ctypes.data, w.ctypes.data, n.ctypes.data, len(w))
+        self.ns = len(w)
+
+    def curve_operators(self, k_s2s=None, k_v2s=None, k_s2v=None, stream=None):
+        """hb_curve_operators into device buffers (column-major; None skips)."""
+        p = (lambda t: None if t is None else _ptr(t))
+        self._call("hb_curve_operators", p(k_s2s), p(k_v2s), p(k_s2v), _stream_ptr(stream))
+
+    def apply_inclusion(self, s, u, nrhs, v2v_dense=False, stream=None):
+        """hb_apply_inclusion: u = (K^{v2v} + K^{s2v} (K^{s2s})^{-1} K^{v2s}) h^2 s."""
+        self._call("hb_apply_inclusion", _ptr(s), _ptr(u), int(nrhs), 1 if v2v_dense else 0,
                    _stream_ptr(stream))
 
     def tree_perm(self):

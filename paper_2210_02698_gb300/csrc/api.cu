@@ -119,6 +119,7 @@ void free_all(hb_ctx* c) {
   hb::dev_free(c->d_tasks[1]);
   hb::flow_plan_free(c->flow_plan[0]);
   hb::flow_plan_free(c->flow_plan[1]);
+  hb::curve_free(c);
   if (c->h_err) cudaFreeHost(c->h_err);
 }
 
@@ -314,6 +315,28 @@ hb_status hb_entries(hb_handle h, const long long* rows, int m, const long long*
     for (int j = 0; j < n; ++j)
       if (cols[j] < 0 || cols[j] >= h->Nv) throw hb::arg_error("column index %lld out of range", cols[j]);
     hb::eval_entries(h, rows, m, cols, n, (double2*)out, (cudaStream_t)stream);
+  });
+}
+
+hb_status hb_curve_set(hb_handle h, const double* centers, const double* lengths, const double* n_seg,
+                       long long ns) {
+  return guarded(h, [&] {
+    if (!h) throw hb::arg_error("null handle");
+    hb::curve_set(h, centers, lengths, n_seg, ns);
+  });
+}
+
+hb_status hb_curve_operators(hb_handle h, void* k_s2s, void* k_v2s, void* k_s2v, void* stream) {
+  return guarded(h, [&] {
+    if (!h) throw hb::arg_error("null handle");
+    hb::curve_operators(h, (double2*)k_s2s, (double2*)k_v2s, (double2*)k_s2v, (cudaStream_t)stream);
+  });
+}
+
+hb_status hb_apply_inclusion(hb_handle h, const void* s, void* u, int nrhs, int v2v_dense, void* stream) {
+  return guarded(h, [&] {
+    check_vec_args(h, s, u, nrhs);
+    hb::apply_inclusion(h, (const double2*)s, (double2*)u, nrhs, v2v_dense, (cudaStream_t)stream);
   });
 }
 

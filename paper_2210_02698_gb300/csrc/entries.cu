@@ -97,17 +97,6 @@ __global__ void self_kernel(const double* __restrict__ ncell, long long Nv, doub
   out[i] = make_double2(-0.25 * Iim / (h * h), 0.25 * Ire / (h * h));
 }
 
-// g = v0 f0 + v1 f1 from interpolated tau^2, v0, v1 (Eq. babich, Eq. termf).
-__device__ __forceinline__ double2 hb_green(double t2, double v0, double v1, double omega) {
-  const double tau = sqrt(fmax(t2, 0.0));
-  const double x = fmax(omega * tau, 1e-12);
-  const Bessel01 b = bessel01(x);
-  const double c = 0.88622692545275801365;         // sqrt(pi)/2
-  const double k1 = c * 2.0 * tau / omega;
-  // f0 = c(-Y0 + i J0),  f1 = k1 (Y1 - i J1)
-  return make_double2(-c * b.y0 * v0 + k1 * b.y1 * v1, c * b.j0 * v0 - k1 * b.j1 * v1);
-}
-
 // Gauss-Legendre nodes/weights on [-1,1] by Newton iteration on P_n.
 static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
   x.resize(n);

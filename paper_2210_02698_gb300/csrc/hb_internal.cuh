@@ -245,6 +245,19 @@ struct hb_ctx {
   double2* d_dense_part = nullptr;
   size_t dense_part_cap = 0;
 
+  // curve inclusion (inclusion.cu): segments and the dense surface operators
+  long long ns = 0;                // segments; 0: no curve set
+  double2* d_seg = nullptr;        // ns centres (x, z)
+  double* d_segw = nullptr;        // ns lengths
+  double* d_segn = nullptr;        // ns values of n at the centres
+  double2* d_cellpts = nullptr;    // N_v cell centres (x, z)
+  double2* d_lu = nullptr;         // K^{s2s} LU-factored in place (ns x ns, column-major)
+  int* d_piv = nullptr;            // its row interchanges
+  double2* d_kv2s = nullptr;       // K^{v2s}, ns x N_v column-major
+  double2* d_ks2v = nullptr;       // K^{s2v}, N_v x ns column-major
+  double2* d_cy = nullptr;         // surface vectors of an apply, ns x cy_cap
+  int cy_cap = 0;
+
   // timing
   bool timing = false;
   std::vector<std::string> tnames;
@@ -285,6 +298,11 @@ void gather_native(const double2* s, const long long* pperm, uint4* x, long long
                    int MT, double scale, cudaStream_t st);
 void apply_bf(hb_ctx* c, const double2* s, double2* u, int nrhs, int adjoint, int precision,
               cudaStream_t st);
+// inclusion.cu
+void curve_set(hb_ctx* c, const double* centers, const double* lengths, const double* n_seg, long long ns);
+void curve_free(hb_ctx* c);
+void curve_operators(hb_ctx* c, double2* k_s2s, double2* k_v2s, double2* k_s2v, cudaStream_t st);
+void apply_inclusion(hb_ctx* c, const double2* s, double2* u, int nrhs, int v2v_dense, cudaStream_t st);
 void tree_build(hb_ctx* c);
 void proxy_rows(const hb_ctx* c, long long t0, long long t1, const long long* seeds, int nseeds,
                 std::vector<long long>& out, std::vector<int>& stamp, int stamp_id);

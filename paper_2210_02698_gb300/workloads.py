@@ -230,6 +230,16 @@ def workload_sources(w: Workload) -> np.ndarray:
     raise ValueError(w.rhs_kind)
 
 
+# ----------------------------------------------------------- inclusions ----
+def circle_segments(center, radius: float, ns: int):
+    """An inclusion's boundary for Sec. 3.2: the circle cut into ns equal
+    chords, returned as (centres (ns, 2) at the chord midpoints, chord
+    lengths (ns,))."""
+    t = np.linspace(0.0, 2.0 * math.pi, ns + 1)
+    p = np.stack([center[0] + radius * np.cos(t), center[1] + radius * np.sin(t)], axis=1)
+    return 0.5 * (p[1:] + p[:-1]), np.hypot(p[1:, 0] - p[:-1, 0], p[1:, 1] - p[:-1, 1])
+
+
 def sample_rows(Nv: int, m: int, seed: int) -> np.ndarray:
     """m distinct seeded row indices (natural order), sorted."""
     rng = np.random.default_rng(seed)
