@@ -160,6 +160,33 @@ def cpu_oracle_sample(w, tables, rows_n, seed=1234):
     return rows, U, dt
 
 
+def one_core_rate(w, rows_n, seed=4321):
+    """The oracle's dense-sum rate (output rows x RHS per second) with its
+    numeric libraries held to one thread: the same sample in a child
+    process whose BLAS / OpenMP thread counts are set to 1 before numpy
+    loads.  Returns (rate, seconds)."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[k] = "1"
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--one-core-sample", w.name, str(rows_n),
+                        str(seed)], env=env, capture_output=True, text=True, timeout=600)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr.strip().splitlines()[-1] if r.stderr.strip() else f"exit {r.returncode}")
+    dt = float(r.stdout.strip().splitlines()[-1])
+    return rows_n * w.nrhs / dt, dt
+
+
+def one_core_entry(w, rows_n):
+    """The one-thread oracle rate as a JSON object (never raises)."""
+    try:
+        rate, dt = one_core_rate(w, rows_n)
+        return {"value": rate, "unit": UNIT, "threads": 1,
+                "sample": f"dense HB sum on {rows_n} seeded rows x all sources x {w.nrhs} RHS, "
+                          f"BLAS/OpenMP held to one thread ({dt:.1f} s)"}
+    except Exception as ex:
+        return {"value": None, "unit": UNIT, "threads": 1, "sample": f"failed: {ex}"}
+
+
 def cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -193,7 +220,8 @@ def run_reference(args):
             "config": {"workload": describe(w), "sample": f"{rows_per_step} seeded output rows x all "
                                    f"{w.grid.Nv} sources x {w.nrhs} RHS per step"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": nc, "kind": "oracle",
-                             "sample": f"dense HB sum (numpy/scipy FP64) on {rows_per_step} rows per step"},
+                             "sample": f"dense HB sum (numpy/scipy FP64) on {rows_per_step} rows per step",
+                             "one_core": one_core_entry(w, rows_per_step)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -404,7 +432,8 @@ def run_ours(args):
             got, got64 = mixed_rows, fp64_rows
             cpu = {"value": rows_n * R / dt, "unit": UNIT, "cores": nc, "kind": "oracle",
                    "sample": f"dense FP64 HB sum, {rows_n} seeded rows x {Nv} sources x {R} RHS "
-                             f"({dt:.1f} s)",
+                             f"({dt:.1f} s; numpy's BLAS threads over all {nc} cores)",
+                   "one_core": one_core_entry(w, max(4, rows_n // 8)),
                    "rel_l2_mixed_vs_oracle": float(np.linalg.norm(got - U_ref) / np.linalg.norm(U_ref)),
                    "rel_l2_fp64_vs_oracle": float(np.linalg.norm(got64 - U_ref) / np.linalg.norm(U_ref))}
             if w.rhs_kind == "mixed64":
@@ -494,8 +523,15 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(W.WORKLOADS))
     ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU oracle leg (profiling runs)")
+    ap.add_argument("--one-core-sample", nargs=3, metavar=("WORKLOAD", "ROWS", "SEED"), help=argparse.SUPPRESS)
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.one_core_sample:
+        # child of one_core_rate: print the seconds of one oracle sample
+        name, rows_n, seed = args.one_core_sample
+        w = W.WORKLOADS[name]
+        _, _, dt = cpu_oracle_sample(w, load_tables(w), int(rows_n), seed=int(seed))
+        print(dt, flush=True)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
