@@ -53,6 +53,22 @@ def test_self_term_lemma_against_brute_force_cell_integral():
         assert abs(kernel.self_term(n0, om, h) - brute) < 1e-9 * abs(brute)
 
 
+def test_self_term_small_cell_closed_form():
+    """As k h -> 0 (k = n0 w), H0(x) = 1 + (2i/pi)(ln(x/2) + gamma_E) + O(x^2 ln x)
+    (A&S 9.1.12-13) averaged over the square cell of side h, where the mean of
+    ln r is ln(h/2) + (ln 2)/2 + pi/4 - 3/2, gives
+    K_ii -> (i/4)(1 + (2i/pi)(ln(k h/4) + gamma_E + (ln 2)/2 + pi/4 - 3/2)),
+    a check of the self term independent of the lemma's theta integral."""
+    gamma = 0.5772156649015329
+    errs = []
+    for kh in (1e-2, 1e-3):
+        n0, h = 0.8, 1 / 64
+        om = kh / (n0 * h)
+        closed = 0.25j * (1 + (2j / math.pi) * (math.log(kh / 4) + gamma + 0.5 * math.log(2) + math.pi / 4 - 1.5))
+        errs.append(abs(kernel.self_term(n0, om, h) - closed) / abs(closed))
+    assert errs[0] < 1e-5 and errs[1] < 1e-7 and errs[0] / errs[1] > 50   # O((k h)^2)
+
+
 def test_homogeneous_entries_exact():
     w = W.WORKLOADS["homog64"]
     tab = tables.build_tables(W.HOMOGENEOUS, 16)
