@@ -122,6 +122,23 @@ def _ptr(t):
     return t.ctypes.data
 
 
+def _device_buf(t, count, name):
+    """Check a buffer the library reads or writes on the device: a CUDA,
+    contiguous complex128 tensor with at least ``count`` elements.  Host
+    arrays are refused; a raw integer address is passed through unchecked."""
+    if isinstance(t, int):
+        return t
+    if not hasattr(t, "data_ptr") or not getattr(t, "is_cuda", False):
+        raise HBError(HB_ERR_ARG, f"{name}: a CUDA tensor is required (got {type(t).__name__})")
+    if str(t.dtype) != "torch.complex128":
+        raise HBError(HB_ERR_ARG, f"{name}: complex128 is required (got {t.dtype})")
+    if not t.is_contiguous():
+        raise HBError(HB_ERR_ARG, f"{name}: a contiguous tensor is required")
+    if t.numel() < count:
+        raise HBError(HB_ERR_ARG, f"{name}: {t.numel()} elements, {count} needed")
+    return t.data_ptr()
+
+
 def _stream_ptr(stream):
     if stream is None:
         return None
@@ -193,23 +210,27 @@ class Operator:
         """Failure-detection self-test of the bounded device waits (see hb.h)."""
         self._call("hb_set_wait_selftest", 1 if on else 0)
 
+    def _vecs(self, a, b, nrhs):
+        n = max(int(nrhs), 0) * self.Nv
+        return _device_buf(a, n, "input"), _device_buf(b, n, "output")
+
     def apply(self, s, u, nrhs, stream=None):
-        self._call("hb_apply", _ptr(s), _ptr(u), int(nrhs), _stream_ptr(stream))
+        self._call("hb_apply", *self._vecs(s, u, nrhs), int(nrhs), _stream_ptr(stream))
 
     def apply_adjoint(self, u, s, nrhs, stream=None):
-        self._call("hb_apply_adjoint", _ptr(u), _ptr(s), int(nrhs), _stream_ptr(stream))
+        self._call("hb_apply_adjoint", *self._vecs(u, s, nrhs), int(nrhs), _stream_ptr(stream))
 
     def apply_dense(self, s, u, nrhs, stream=None):
-        self._call("hb_apply_dense", _ptr(s), _ptr(u), int(nrhs), _stream_ptr(stream))
+        self._call("hb_apply_dense", *self._vecs(s, u, nrhs), int(nrhs), _stream_ptr(stream))
 
     def apply_dense_adjoint(self, u, s, nrhs, stream=None):
-        self._call("hb_apply_dense_adjoint", _ptr(u), _ptr(s), int(nrhs), _stream_ptr(stream))
+        self._call("hb_apply_dense_adjoint", *self._vecs(u, s, nrhs), int(nrhs), _stream_ptr(stream))
 
     def entries(self, rows, cols, out, stream=None):
         rows = np.ascontiguousarray(rows, dtype=np.int64)
         cols = np.ascontiguousarray(cols, dtype=np.int64)
-        self._call("hb_entries", rows.ctypes.data, len(rows), cols.ctypes.data, len(cols), _ptr(out),
-                   _stream_ptr(stream))
+        self._call("hb_entries", rows.ctypes.data, len(rows), cols.ctypes.data, len(cols),
+                   _device_buf(out, len(rows) * len(cols), "out"), _stream_ptr(stream))
 
     def set_curve(self, centers, lengths, n_seg):
         """hb_curve_set: the inclusion's segments (centres (ns, 2), lengths,
@@ -224,12 +245,14 @@ class Operator:
 
     def curve_operators(self, k_s2s=None, k_v2s=None, k_s2v=None, stream=None):
         """hb_curve_operators into device buffers (column-major; None skips)."""
-        p = (lambda t: None if t is None else _ptr(t))
-        self._call("hb_curve_operators", p(k_s2s), p(k_v2s), p(k_s2v), _stream_ptr(stream))
+        ns = getattr(self, "ns", 0)
+        p = (lambda t, n, name: None if t is None else _device_buf(t, n, name))
+        self._call("hb_curve_operators", p(k_s2s, ns * ns, "k_s2s"), p(k_v2s, ns * self.Nv, "k_v2s"),
+                   p(k_s2v, ns * self.Nv, "k_s2v"), _stream_ptr(stream))
 
     def apply_inclusion(self, s, u, nrhs, v2v_dense=False, stream=None):
         """hb_apply_inclusion: u = (K^{v2v} + K^{s2v} (K^{s2s})^{-1} K^{v2s}) h^2 s."""
-        self._call("hb_apply_inclusion", _ptr(s), _ptr(u), int(nrhs), 1 if v2v_dense else 0,
+        self._call("hb_apply_inclusion", *self._vecs(s, u, nrhs), int(nrhs), 1 if v2v_dense else 0,
                    _stream_ptr(stream))
 
     def tree_perm(self):

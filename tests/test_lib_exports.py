@@ -77,3 +77,34 @@ def test_device_alloc_cap_is_host_state(L):
         assert binding.device_alloc_cap(-1) == live
     finally:
         binding.device_alloc_cap(0)
+
+
+def test_device_buffers_are_checked_before_any_call():
+    """The binding refuses buffers the library would read as device
+    complex128 memory: host arrays, CPU tensors, other dtypes, strided
+    views, too few elements (HB_ERR_ARG before the library is called)."""
+    import torch
+    from paper_2210_02698_gb300 import binding
+
+    class FakeCuda:
+        """Stands for a CUDA tensor (none exists on this host)."""
+        def __init__(self, dtype="torch.complex128", contiguous=True, numel=8):
+            self.is_cuda, self.dtype, self._c, self._n = True, dtype, contiguous, numel
+
+        def data_ptr(self):
+            return 4096
+
+        def is_contiguous(self):
+            return self._c
+
+        def numel(self):
+            return self._n
+
+    assert binding._device_buf(FakeCuda(), 8, "s") == 4096
+    assert binding._device_buf(1234, 8, "s") == 1234          # a raw address passes unchecked
+    bad = [np.zeros(8, dtype=np.complex128), torch.zeros(8, dtype=torch.complex128),
+           FakeCuda(dtype="torch.complex64"), FakeCuda(contiguous=False), FakeCuda(numel=7), None]
+    for b in bad:
+        with pytest.raises(binding.HBError) as e:
+            binding._device_buf(b, 8, "s")
+        assert e.value.status == binding.HB_ERR_ARG
