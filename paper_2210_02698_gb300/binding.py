@@ -115,23 +115,16 @@ def _check(st, handle=None):
         raise HBError(st, lib().hb_last_error(handle).decode(errors="replace"))
 
 
-def _ptr(t):
-    """Device/host address of a torch tensor or numpy array."""
-    if hasattr(t, "data_ptr"):
-        return t.data_ptr()
-    return t.ctypes.data
-
-
-def _device_buf(t, count, name):
+def _device_buf(t, count, name, dtype="torch.complex128"):
     """Check a buffer the library reads or writes on the device: a CUDA,
-    contiguous complex128 tensor with at least ``count`` elements.  Host
+    contiguous tensor of ``dtype`` with at least ``count`` elements.  Host
     arrays are refused; a raw integer address is passed through unchecked."""
     if isinstance(t, int):
         return t
     if not hasattr(t, "data_ptr") or not getattr(t, "is_cuda", False):
         raise HBError(HB_ERR_ARG, f"{name}: a CUDA tensor is required (got {type(t).__name__})")
-    if str(t.dtype) != "torch.complex128":
-        raise HBError(HB_ERR_ARG, f"{name}: complex128 is required (got {t.dtype})")
+    if str(t.dtype) != dtype:
+        raise HBError(HB_ERR_ARG, f"{name}: {dtype[6:]} is required (got {t.dtype})")
     if not t.is_contiguous():
         raise HBError(HB_ERR_ARG, f"{name}: a contiguous tensor is required")
     if t.numel() < count:
@@ -287,22 +280,36 @@ class Operator:
         return {bytes(names[i]).split(b"\0")[0].decode(): (ms[i], cnt[i]) for i in range(min(ng.value, cap))}
 
 
-def id_batch(A, m, n, a_off, eps, rank, skel, V):
-    """hb_id_batch on device buffers (torch tensors) with host size arrays."""
+def _id_args(A, m, n, a_off, rank, skel, V):
+    """Host size arrays and checked device buffers of hb_id_batch(_noalloc):
+    A (complex128) must hold every matrix, rank (int32) one entry per matrix,
+    skel (int32) sum(n), V (complex128) sum(n^2)."""
     m = np.ascontiguousarray(m, dtype=np.int32)
     n = np.ascontiguousarray(n, dtype=np.int32)
     a_off = np.ascontiguousarray(a_off, dtype=np.int64)
-    _check(lib().hb_id_batch(len(m), m.ctypes.data, n.ctypes.data, a_off.ctypes.data, _ptr(A),
-                             float(eps), _ptr(rank), _ptr(skel), _ptr(V)))
+    if not (len(m) == len(n) == len(a_off)):
+        raise HBError(HB_ERR_ARG, "m, n and a_off differ in length")
+    cnt = len(m)
+    a_need = int(np.max(a_off + m.astype(np.int64) * n)) if cnt else 0
+    n64 = n.astype(np.int64)
+    ptrs = (_device_buf(A, a_need, "A"), _device_buf(rank, cnt, "rank", "torch.int32"),
+            _device_buf(skel, int(n64.sum()), "skel", "torch.int32"),
+            _device_buf(V, int((n64 * n64).sum()), "V"))
+    return m, n, a_off, ptrs
+
+
+def id_batch(A, m, n, a_off, eps, rank, skel, V):
+    """hb_id_batch on device buffers (torch tensors) with host size arrays."""
+    m, n, a_off, (pA, pr, ps, pV) = _id_args(A, m, n, a_off, rank, skel, V)
+    _check(lib().hb_id_batch(len(m), m.ctypes.data, n.ctypes.data, a_off.ctypes.data, pA,
+                             float(eps), pr, ps, pV))
 
 
 def id_batch_noalloc(A, m, n, a_off, eps, rank, skel, V, stream=None):
     """hb_id_batch_noalloc: hb_id_batch without any device allocation."""
-    m = np.ascontiguousarray(m, dtype=np.int32)
-    n = np.ascontiguousarray(n, dtype=np.int32)
-    a_off = np.ascontiguousarray(a_off, dtype=np.int64)
-    _check(lib().hb_id_batch_noalloc(len(m), m.ctypes.data, n.ctypes.data, a_off.ctypes.data, _ptr(A),
-                                     float(eps), _ptr(rank), _ptr(skel), _ptr(V), _stream_ptr(stream)))
+    m, n, a_off, (pA, pr, ps, pV) = _id_args(A, m, n, a_off, rank, skel, V)
+    _check(lib().hb_id_batch_noalloc(len(m), m.ctypes.data, n.ctypes.data, a_off.ctypes.data, pA,
+                                     float(eps), pr, ps, pV, _stream_ptr(stream)))
 
 
 def load_tables(path):

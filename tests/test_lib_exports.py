@@ -108,3 +108,45 @@ def test_device_buffers_are_checked_before_any_call():
         with pytest.raises(binding.HBError) as e:
             binding._device_buf(b, 8, "s")
         assert e.value.status == binding.HB_ERR_ARG
+
+
+def test_id_batch_buffers_checked_as_the_gpu_tests_build_them():
+    """The size rules of the ID entry points accept buffers built exactly
+    as the GPU tests build them (CPU tensors standing in for CUDA ones) and
+    refuse a short or mistyped one."""
+    import torch
+    from paper_2210_02698_gb300 import binding, workloads as W
+
+    class AsCuda:
+        def __init__(self, t):
+            self.t, self.is_cuda, self.dtype = t, True, t.dtype
+
+        def data_ptr(self):
+            return self.t.data_ptr()
+
+        def is_contiguous(self):
+            return self.t.is_contiguous()
+
+        def numel(self):
+            return self.t.numel()
+
+    rng = np.random.default_rng(3)
+    a = rng.standard_normal(10) + 1j * rng.standard_normal(10)
+    A3 = W.random_id_matrices(3, 37, 90, 25, 0.5, seed=12)
+    mats = [np.stack([a, a, 0.5 * a], axis=1), np.zeros((5, 4), dtype=complex),
+            rng.standard_normal((1, 6)) + 0j] + [A3[b].T.copy() for b in range(3)]
+    m = np.array([x.shape[0] for x in mats], dtype=np.int32)
+    n = np.array([x.shape[1] for x in mats], dtype=np.int32)
+    off = np.concatenate([[0], np.cumsum(m.astype(np.int64) * n)[:-1]]).astype(np.int64)
+    A = torch.from_numpy(np.concatenate([x.T.reshape(-1) for x in mats]))
+    rank = torch.zeros(len(mats), dtype=torch.int32)
+    skel = torch.zeros(int(n.sum()), dtype=torch.int32)
+    V = torch.zeros(int((n.astype(np.int64) ** 2).sum()), dtype=torch.complex128)
+    bufs = [AsCuda(t) for t in (A, rank, skel, V)]
+    binding._id_args(bufs[0], m, n, off, *bufs[1:])
+    for k, bad in enumerate([A[:-1], rank.to(torch.int64), skel[:-1], V.to(torch.complex64)]):
+        b = list(bufs)
+        b[k] = AsCuda(bad)
+        with pytest.raises(binding.HBError) as e:
+            binding._id_args(b[0], m, n, off, *b[1:])
+        assert e.value.status == binding.HB_ERR_ARG
