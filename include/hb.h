@@ -304,6 +304,16 @@ hb_status hb_proxy_rows(hb_handle h, long long t0, long long t1, const long long
 
 hb_status hb_info(hb_handle h, hb_stats* stats);
 
+/* hb_rank_profile: the ranks r_{tau,nu} of the built HODBF by HODBF level l
+ * (the 2^l butterflies between sibling clusters of level l, l = 1..L_v) and
+ * butterfly level k (k = 0: V^0; k = 1..L_v - l: W^k, the last also giving
+ * K^L's columns).  max_rank (int) and mean_rank (double) are HOST arrays of
+ * (L_v + 1) x (L_v + 1) entries, row-major [l][k]; entries without blocks
+ * (l = 0, k > L_v - l) are 0.  Sec. 4.2.2 relates them to the cluster sizes:
+ * bounded away from the middle level, growing near it.  Synchronous (host
+ * data only).  Errors: HB_ERR_STATE before hb_build. */
+hb_status hb_rank_profile(hb_handle h, int* max_rank, double* mean_rank);
+
 /* hb_kernel_times: enable (1) / disable (0) CUDA-event timing of every
  * kernel launched by hb_apply / hb_apply_adjoint on the launch stream, and
  * read back the accumulated per-kernel-group totals: names, total ms and

@@ -25,7 +25,7 @@ EXPORTS = ["hb_create", "hb_build", "hb_save", "hb_load", "hb_apply", "hb_apply_
            "hb_set_wait_selftest", "hb_device_alloc_cap",
            "hb_apply_dense", "hb_apply_dense_adjoint", "hb_entries", "hb_curve_set", "hb_curve_operators",
            "hb_apply_inclusion", "hb_id_batch", "hb_id_batch_noalloc",
-           "hb_tree_perm", "hb_proxy_rows", "hb_info", "hb_set_kernel_timing",
+           "hb_tree_perm", "hb_proxy_rows", "hb_info", "hb_rank_profile", "hb_set_kernel_timing",
            "hb_kernel_times", "hb_last_error", "hb_destroy"]
 
 
@@ -83,6 +83,7 @@ def lib():
         L.hb_tree_perm.argtypes = [vp, vp]
         L.hb_proxy_rows.argtypes = [vp, ll, ll, vp, i, vp, vp]
         L.hb_info.argtypes = [vp, C.POINTER(Stats)]
+        L.hb_rank_profile.argtypes = [vp, vp, vp]
         L.hb_set_kernel_timing.argtypes = [vp, i]
         L.hb_kernel_times.argtypes = [vp, i, vp, vp, vp, vp]
         L.hb_last_error.argtypes = [vp]
@@ -265,6 +266,15 @@ class Operator:
         s = Stats()
         self._call("hb_info", C.byref(s))
         return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+    def rank_profile(self):
+        """hb_rank_profile: (max, mean) ranks as (L_v+1, L_v+1) arrays indexed
+        [HODBF level l][butterfly level k]."""
+        n = int(self.info()["levels"]) + 1
+        mx = np.zeros((n, n), dtype=np.int32)
+        mean = np.zeros((n, n), dtype=np.float64)
+        self._call("hb_rank_profile", mx.ctypes.data, mean.ctypes.data)
+        return mx, mean
 
     def set_kernel_timing(self, on):
         self._call("hb_set_kernel_timing", 1 if on else 0)

@@ -318,6 +318,28 @@ hb_status hb_entries(hb_handle h, const long long* rows, int m, const long long*
   });
 }
 
+hb_status hb_rank_profile(hb_handle h, int* max_rank, double* mean_rank) {
+  return guarded(h, [&] {
+    if (!h || !max_rank || !mean_rank) throw hb::arg_error("null argument");
+    if (!h->built) throw hb::Error{HB_ERR_STATE, "hb_rank_profile before hb_build"};
+    const int n = h->Lv + 1;
+    std::vector<long long> sum((size_t)n * n, 0), cnt((size_t)n * n, 0);
+    std::fill(max_rank, max_rank + (size_t)n * n, 0);
+    for (const hb::BflyIndex& b : h->bidx) {
+      if (b.l < 1 || b.l > h->Lv || b.L < 0 || b.l + b.L > h->Lv || (int)b.rank.size() != b.L + 1)
+        throw hb::Error{HB_ERR_STATE, "inconsistent factor index"};
+      for (int k = 0; k <= b.L; ++k)
+        for (int r : b.rank[(size_t)k]) {
+          const size_t at = (size_t)b.l * n + k;
+          max_rank[at] = std::max(max_rank[at], r);
+          sum[at] += r;
+          cnt[at] += 1;
+        }
+    }
+    for (size_t i = 0; i < (size_t)n * n; ++i) mean_rank[i] = cnt[i] ? (double)sum[i] / (double)cnt[i] : 0.0;
+  });
+}
+
 hb_status hb_curve_set(hb_handle h, const double* centers, const double* lengths, const double* n_seg,
                        long long ns) {
   return guarded(h, [&] {

@@ -25,6 +25,9 @@ def test_save_load_roundtrip_and_oracle_file_apply(tmp_path):
     with pytest.raises(binding.HBError) as e:
         op.save(tmp_path / "early.hbf")
     assert e.value.status == binding.HB_ERR_STATE
+    with pytest.raises(binding.HBError) as e:
+        op.rank_profile()
+    assert e.value.status == binding.HB_ERR_STATE
     op.build()
     path = tmp_path / "op.hbf"
     op.save(path)
@@ -49,6 +52,22 @@ def test_save_load_roundtrip_and_oracle_file_apply(tmp_path):
     assert np.array_equal(run(ld), umx)
 
     F = FactorFile(path)
+    # ranks by HODBF level l and butterfly level k: the library's profile
+    # against the ranks the file holds
+    n = F.Lv + 1
+    fmx, fsum, fcnt = np.zeros((n, n), dtype=np.int64), np.zeros((n, n)), np.zeros((n, n))
+    for b in F.butterflies:
+        for k in range(int(b["L"]) + 1):
+            r = np.asarray(b["rank"][k], dtype=np.int64)
+            l = int(b["l"])
+            fmx[l, k] = max(fmx[l, k], int(r.max()))
+            fsum[l, k] += r.sum()
+            fcnt[l, k] += len(r)
+    mx, mean = op.rank_profile()
+    assert np.array_equal(mx, fmx) and mx.max() == op.info()["max_rank"]
+    assert np.allclose(mean, np.divide(fsum, fcnt, out=np.zeros_like(fsum), where=fcnt > 0), rtol=1e-14, atol=0)
+    lmx, lmean = ld.rank_profile()
+    assert np.array_equal(lmx, mx) and np.array_equal(lmean, mean)
     assert rel_l2(F.apply(s), u64) < 1e-13
     assert rel_l2(F.apply_adjoint(s), a64) < 1e-13
     assert rel_l2(F.apply(s), dense.apply(oracle_op(w), s)) < 1e-5
