@@ -25,6 +25,10 @@ Modules (each function cites the passage it follows):
 * ``inclusion`` - scattering by a curve inclusion (Sec. 3.2): K^{s2s},
   K^{v2s}, K^{s2v} and the total field of Eq. m_v2v_inclu, with the exact
   circle series that pins them.
+* ``hb3d``      - the ansatz with d = 3 (half-order f_q), the paper's 3D
+  media, closed-form tau, v0, v1 and the exact Green's function of the 3D
+  constant-gradient medium (Sec. 5.1.2), the 3D self term (Appendix A.2):
+  groundwork for a 3D path.
 * ``hankel``    - the Hankel-type functions f_q (Eq. termf).
 * ``kernel``    - matrix entries g = v0 f0 + v1 f1 (Eq. babich) and the 2D
   self term (Appendix A, Eq. HankelIntegral2dlemma).

@@ -230,6 +230,57 @@ def workload_sources(w: Workload) -> np.ndarray:
     raise ValueError(w.rhs_kind)
 
 
+# ------------------------------------------------------------------ 3D ----
+@dataclass(frozen=True)
+class Medium3D:
+    """Refractive index n(r) of the paper's 3D examples (Sec. 5.1.2).
+
+    kind = "homogeneous": n = n0.
+    kind = "gradient":    n = a / (c - y), i.e. velocity 1/n linear in y with
+                          gradient -1/a (a = 1.25, c = 0.885 on [0, 0.52]^3).
+    """
+
+    kind: str
+    n0: float = 1.0
+    a: float = 1.25
+    c: float = 0.885
+
+    def n(self, x, y, z):
+        x, y, z = (np.asarray(v, dtype=np.float64) for v in (x, y, z))
+        shape = np.broadcast(x, y, z).shape
+        if self.kind == "homogeneous":
+            return np.full(shape, self.n0)
+        if self.kind == "gradient":
+            return np.broadcast_to(self.a / (self.c - y), shape).copy()
+        raise ValueError(self.kind)
+
+
+HOMOGENEOUS_3D = Medium3D("homogeneous")
+GRADIENT_3D = Medium3D("gradient")
+
+
+@dataclass(frozen=True)
+class Grid3D:
+    """N^3 cells of side h = L/N on [0, L]^3; natural index (c N + b) N + a
+    with a the x index (fastest), b the y index, c the z index."""
+
+    N: int
+    L: float = 1.0
+
+    @property
+    def h(self) -> float:
+        return self.L / self.N
+
+    @property
+    def Nv(self) -> int:
+        return self.N ** 3
+
+    def centroids(self):
+        t = (np.arange(self.N) + 0.5) * self.h
+        z, y, x = np.meshgrid(t, t, t, indexing="ij")
+        return x.reshape(-1), y.reshape(-1), z.reshape(-1)
+
+
 # ----------------------------------------------------------- inclusions ----
 def circle_segments(center, radius: float, ns: int):
     """An inclusion's boundary for Sec. 3.2: the circle cut into ns equal
