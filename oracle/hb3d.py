@@ -41,11 +41,19 @@ side h around r_i, divided by h^3 (the 3D counterpart of the 2D reading
 K_ii = (cell integral of g) / h^2, since U = K (s h^d)).  Written out: the
 radial integral of e^{i k r} r in closed form, k = n0 w, times the angular
 integral over the 48 congruent pieces of the cube, by adaptive quadrature.
+
+Tables and entries (Sec. 4.1 in 3D): tau^2, v0, v1 at all pairs of the n_I^3
+tensor Chebyshev nodes of the box (row = observation node, node index
+i = (i3 n_I + i2) n_I + i1, x fastest), interpolated at cell centres by
+T^o F^c T^s with T_i(r) = l_{i1}(x) l_{i2}(y) l_{i3}(z) (Eq. chebinterpblock);
+the dense sum U = K I, I = s h^3, on N^3 cells (Eq. m_v2v with d = 3).
 """
 import math
 
 import numpy as np
 from scipy import integrate, special
+
+from . import chebyshev
 
 
 # ------------------------------------------------------------- f_q, d = 3 ----
@@ -165,3 +173,74 @@ def cube_integral(k, h):
 def self_term(n0, omega, h):
     """K_ii = (1/h^3) int_cube n0 e^{i w tau} / (4 pi tau) dV, tau = n0 r."""
     return cube_integral(n0 * omega, h) / h ** 3
+
+
+# ------------------------------------------------ tables and entries ----
+def tensor_basis3(xn, px, py, pz):
+    """T_i(r) = l_{i1}(x) l_{i2}(y) l_{i3}(z), i = (i3 n_I + i2) n_I + i1;
+    shape (len(p), n_I^3)."""
+    Lx, Ly, Lz = (chebyshev.lagrange(xn, p) for p in (px, py, pz))
+    n = len(xn)
+    return (Lz[:, :, None, None] * Ly[:, None, :, None] * Lx[:, None, None, :]).reshape(len(Lx), n ** 3)
+
+
+def node_points3(xn):
+    """The n_I^3 tensor nodes (x fastest), shape (n_I^3, 3)."""
+    Z, Y, X = np.meshgrid(xn, xn, xn, indexing="ij")
+    return np.stack([X.reshape(-1), Y.reshape(-1), Z.reshape(-1)], axis=1)
+
+
+def build_tables3(medium, n_I, L):
+    """tau^2, v0, v1 at all node pairs of the box [0, L]^3 from the exact
+    ingredients (the diagonal: tau^2 = 0, v0 = n0 / (2 pi), v1 its limit)."""
+    xn = L * chebyshev.nodes(n_I)
+    P = node_points3(xn)
+    r, r0 = P[:, None, :], P[None, :, :]
+    return {"nodes": xn, "n_I": n_I, "L": L, "tau2": tau(medium, r, r0) ** 2,
+            "v0": v0(medium, r, r0), "v1": v1(medium, r, r0)}
+
+
+class Operator3:
+    """K on the N^3 cell centres of a Grid3D: interpolated ingredients off the
+    diagonal (Eq. chebinterpblock, Eq. babich with d = 3, N = 1), the 3D self
+    term on it."""
+
+    def __init__(self, grid, tab, omega, medium):
+        self.grid, self.tab, self.omega, self.medium = grid, tab, omega, medium
+        self.h, self.Nv = grid.h, grid.Nv
+        x, y, z = grid.centroids()
+        self.pts = np.stack([x, y, z], axis=1)
+        self.n_cells = medium.n(x, y, z)
+        self._self = {}
+
+    def self_term(self, i):
+        n0 = float(self.n_cells[i])
+        if n0 not in self._self:
+            self._self[n0] = self_term(n0, self.omega, self.h)
+        return self._self[n0]
+
+    def block(self, rows, cols):
+        rows, cols = np.asarray(rows), np.asarray(cols)
+        xn = self.tab["nodes"]
+        To = tensor_basis3(xn, *self.pts[rows].T)
+        Ts = tensor_basis3(xn, *self.pts[cols].T)
+        t2, a0, a1 = (chebyshev.interp_block(self.tab[q], To, Ts) for q in ("tau2", "v0", "v1"))
+        diag = rows[:, None] == cols[None, :]
+        t = np.where(diag, 1.0, np.sqrt(np.maximum(t2, 0.0)))
+        K = kernel(self.omega, t, (a0, a1))
+        for a, b in zip(*np.nonzero(diag)):
+            K[a, b] = self.self_term(rows[a])
+        return K
+
+
+def dense_apply3(op, s, rows=None, chunk=512):
+    """U_i = sum_j K_ij I_j, I = s h^3 (Eq. m_v2v, d = 3)."""
+    s = np.asarray(s, dtype=np.complex128)
+    s = s[:, None] if s.ndim == 1 else s
+    rows = np.arange(op.Nv) if rows is None else np.asarray(rows)
+    I = s * op.h ** 3
+    U = np.zeros((len(rows), s.shape[1]), dtype=np.complex128)
+    for c0 in range(0, op.Nv, chunk):
+        cols = np.arange(c0, min(op.Nv, c0 + chunk))
+        U += op.block(rows, cols) @ I[cols]
+    return U

@@ -6,7 +6,7 @@ import math
 import numpy as np
 import pytest
 
-from oracle import hb3d
+from oracle import chebyshev, hb3d
 from paper_2210_02698_gb300 import workloads as W
 
 GR = W.GRADIENT_3D
@@ -138,3 +138,60 @@ def test_cube_integral_against_cartesian_quadrature():
         got = hb3d.cube_integral(k, h)
         assert abs(got - want) < 1e-6 * abs(want)
 
+
+
+def test_tables_homogeneous_interpolate_exactly():
+    """tau^2 = n0^2 |r - r0|^2 has degree 2 in each coordinate, so the 3D
+    tensor interpolation (n_I >= 3) reproduces it and the entries equal
+    e^{i k R}/(4 pi R) off the diagonal; the diagonal is the cube integral."""
+    med = W.Medium3D("homogeneous", n0=1.1)
+    g = W.Grid3D(6, 0.5)
+    w = 2 * math.pi * 4
+    op = hb3d.Operator3(g, hb3d.build_tables3(med, 4, g.L), w, med)
+    idx = np.arange(g.Nv)
+    K = op.block(idx, idx)
+    P = op.pts
+    R = np.linalg.norm(P[:, None, :] - P[None, :, :], axis=-1)
+    off = ~np.eye(g.Nv, dtype=bool)
+    want = np.exp(1j * w * 1.1 * R[off]) / (4 * math.pi * R[off])
+    assert np.max(np.abs(K[off] - want) / np.abs(want)) < 1e-11
+    assert np.allclose(np.diag(K), hb3d.cube_integral(1.1 * w, g.h) / g.h ** 3, rtol=1e-14, atol=0)
+
+
+def test_tables_gradient_interpolation_converges():
+    """Interpolated tau^2 and v0 of the gradient medium at random point pairs
+    of [0, 0.52]^3 converge to the closed forms as n_I grows (a transposed or
+    misordered node index would stay O(1) wrong)."""
+    rng = np.random.default_rng(4)
+    ro, rs = rng.uniform(0, 0.52, size=(40, 3)), rng.uniform(0, 0.52, size=(40, 3))
+    errs = []
+    for n_I in (3, 5, 7):
+        tab = hb3d.build_tables3(GR, n_I, 0.52)
+        To = hb3d.tensor_basis3(tab["nodes"], *ro.T)
+        Ts = hb3d.tensor_basis3(tab["nodes"], *rs.T)
+        t2 = np.einsum("ai,ij,aj->a", To, tab["tau2"], Ts)
+        a0 = np.einsum("ai,ij,aj->a", To, tab["v0"], Ts)
+        e_t2 = np.max(np.abs(t2 - hb3d.tau(GR, ro, rs) ** 2))
+        e_v0 = np.max(np.abs(a0 - hb3d.v0(GR, ro, rs)) / hb3d.v0(GR, ro, rs))
+        errs.append(max(e_t2, e_v0))
+    assert errs[0] / errs[1] > 10 and errs[1] / errs[2] > 10 and errs[2] < 3e-4   # spectral: ~20x per 2 nodes
+
+
+def test_dense_sum_is_the_matrix_product():
+    """U = K (s h^3) in column chunks equals the full matrix product."""
+    g = W.Grid3D(4, 0.52)
+    op = hb3d.Operator3(g, hb3d.build_tables3(GR, 5, g.L), 2 * math.pi * 3, GR)
+    s = W.complex_normal_sources(g.Nv, 2, 9)
+    idx = np.arange(g.Nv)
+    full = op.block(idx, idx) @ (s * g.h ** 3)
+    assert np.allclose(hb3d.dense_apply3(op, s, chunk=7), full, rtol=1e-13, atol=0)
+
+
+def test_tensor_basis_is_cardinal_at_the_nodes():
+    """T_i(r^c_j) = delta_ij with the node order of the tables (x fastest):
+    catches a basis whose axis order disagrees with the node layout (the 3D
+    media are symmetric under x <-> z, so interpolation alone cannot)."""
+    xn = 0.52 * chebyshev.nodes(3)
+    P = hb3d.node_points3(xn)
+    assert np.allclose(hb3d.tensor_basis3(xn, *P.T), np.eye(len(P)), atol=1e-13)
+    assert np.allclose(P[1], [xn[1], xn[0], xn[0]]) and np.allclose(P[3], [xn[0], xn[1], xn[0]])
