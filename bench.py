@@ -187,6 +187,20 @@ def one_core_entry(w, rows_n):
         return {"value": None, "unit": UNIT, "threads": 1, "sample": f"failed: {ex}"}
 
 
+def rank_summary(op):
+    """Ranks of the built HODBF (hb_rank_profile): the largest rank at each
+    HODBF level l = 1..L_v, and the largest and mean rank at each butterfly
+    level k of the top-level (l = 1) butterflies.  Never raises."""
+    try:
+        mx, mean = op.rank_profile()
+        Lv = mx.shape[0] - 1
+        return {"max_by_hodbf_level": [int(mx[l].max()) for l in range(1, Lv + 1)],
+                "top_level_max_by_butterfly_level": [int(v) for v in mx[1, :Lv]],
+                "top_level_mean_by_butterfly_level": [round(float(v), 2) for v in mean[1, :Lv]]}
+    except Exception as ex:
+        return {"failed": str(ex)}
+
+
 def cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -505,6 +519,7 @@ def run_ours(args):
             "factor_bytes": {"fp64": info["factor_bytes_fp64"], "mixed_per_direction": info["factor_bytes_mixed"],
                              "total_device": info["factor_bytes_fp64"] + 2 * info["factor_bytes_mixed"]},
             "max_rank": info["max_rank"],
+            "ranks": rank_summary(op),
             "kernel_ms_per_apply": {k: v[0] / nk for k, v in ktimes.items()},
             **({"autograd": autograd_line} if autograd_line else {}),
             "gather_scatter_ms": gather_ms,
