@@ -25,6 +25,9 @@ Modules (each function cites the passage it follows):
 * ``inclusion`` - scattering by a curve inclusion (Sec. 3.2): K^{s2s},
   K^{v2s}, K^{s2v} and the total field of Eq. m_v2v_inclu, with the exact
   circle series that pins them.
+* ``curve_butterfly`` - K^{s2v} as a single butterfly between the cell tree
+  and a K-D tree of the segments (Sec. 4.2, K^{s2v} item): a prototype of
+  the compressed surface operators, checked against ``inclusion``.
 * ``hb3d``      - the ansatz with d = 3 (half-order f_q), the paper's 3D
   media, closed-form tau, v0, v1 and the exact Green's function of the 3D
   constant-gradient medium (Sec. 5.1.2), the 3D self term (Appendix A.2):
