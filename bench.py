@@ -114,6 +114,7 @@ class Clocks:
 
 
 PROFILE = os.path.join(ROOT, "profiles", "bf_step_kernel_grad256.md")
+PROFILE_WORKLOAD = "grad256"      # the workload the ncu summary was captured on
 KERNEL_SOURCES = ["paper_2210_02698_gb300/csrc/bf_mma.cu", "paper_2210_02698_gb300/csrc/build.cu"]
 
 
@@ -126,9 +127,12 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
+def profiled_traffic(workload):
     """DRAM bytes (read + write) of the step kernels of one apply from the
-    committed ncu summary, if it was taken on the current kernel sources."""
+    committed ncu summary, if it was taken on the current kernel sources and
+    on this workload (None otherwise)."""
+    if workload != PROFILE_WORKLOAD:
+        return None
     try:
         with open(PROFILE) as f:
             txt = f.read()
@@ -494,7 +498,7 @@ def run_ours(args):
                                     "tensor-core products per complex MAC, FP32 accumulate, FP64 output",
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": profiled_traffic(),
+                         "frac": achieved / hbm, "traffic": profiled_traffic(args.workload),
                          "kernel": "butterfly step kernels of one apply (one launch per dependency depth)",
                          "alg_bytes": alg_bytes, "kernel_ms": step_ms,
                          "peak_kind": f"{peak_kind} copy bandwidth"},
