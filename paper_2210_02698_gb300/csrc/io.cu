@@ -27,10 +27,25 @@ const char kMagic[8] = {'H', 'B', 'F', 'A', 'C', 'T', '0', '1'};
 struct File {
   FILE* f = nullptr;
   std::string path;
+  long long size = -1;   // bytes in the file (reading); -1: unknown
   ~File() {
     if (f) fclose(f);
   }
 };
+
+// Bytes left to read; a count read from the file is checked against it
+// before anything is allocated for it.
+long long remaining(File& F) {
+  if (F.size < 0) return -1;
+  const long pos = ftell(F.f);
+  return pos < 0 ? -1 : F.size - (long long)pos;
+}
+
+void need(File& F, long long count, size_t elem) {
+  const long long left = remaining(F);
+  if (count < 0 || (left >= 0 && (unsigned long long)count > (unsigned long long)left / elem))
+    throw Error{HB_ERR_ARG, "truncated or corrupt factor file " + F.path};
+}
 
 void put_raw(File& F, const void* p, size_t bytes) {
   if (bytes && fwrite(p, 1, bytes, F.f) != bytes)
@@ -64,6 +79,7 @@ long long get_count(File& F, long long lo, long long hi, const char* what) {
 }
 template <class T>
 std::vector<T> get_vec(File& F, long long n) {
+  need(F, n, sizeof(T));
   std::vector<T> v((size_t)n);
   get_raw(F, v.data(), (size_t)n * sizeof(T));
   return v;
@@ -132,6 +148,11 @@ hb_ctx* load_file(const char* path,
   F.path = path;
   F.f = fopen(path, "rb");
   if (!F.f) throw Error{HB_ERR_ARG, std::string("cannot open ") + path};
+  if (fseek(F.f, 0, SEEK_END) == 0) {
+    const long end = ftell(F.f);
+    F.size = end < 0 ? -1 : (long long)end;
+  }
+  if (fseek(F.f, 0, SEEK_SET) != 0) throw Error{HB_ERR_ARG, std::string("cannot read ") + path};
   char magic[8];
   get_raw(F, magic, sizeof magic);
   if (std::memcmp(magic, kMagic, sizeof magic) != 0) throw Error{HB_ERR_ARG, "not an HB factor file"};
@@ -174,6 +195,7 @@ hb_ctx* load_file(const char* path,
     if (get_vec<long long>(F, (1LL << l) + 1) != c->bounds[(size_t)l])
       throw Error{HB_ERR_ARG, "factor file: tree nodes differ"};
   c->n_factor = get_count(F, 0, 1LL << 40, "arena size");
+  need(F, c->n_factor, sizeof(double2));
   c->d_f64 = dev_alloc<double2>((size_t)c->n_factor + 16);
   HB_CUDA(cudaMemset(c->d_f64, 0, sizeof(double2) * ((size_t)c->n_factor + 16)));
   {

@@ -150,3 +150,40 @@ def test_id_batch_buffers_checked_as_the_gpu_tests_build_them():
         with pytest.raises(binding.HBError) as e:
             binding._id_args(b[0], m, n, off, *b[1:])
         assert e.value.status == binding.HB_ERR_ARG
+
+
+def test_factor_file_reader_rejects_corrupt_files_without_a_device(L, tmp_path):
+    """hb_load parses the whole header before it needs a device, so on this
+    host a valid file reaches the device check (HB_ERR_CUDA; HB_OK where a
+    GPU exists) while truncated files and corrupt counts are refused with
+    HB_ERR_ARG - a count larger than the file is refused before anything is
+    allocated for it."""
+    import torch
+    from paper_2210_02698_gb300 import binding
+    from tests.test_oracle_factor_file import _write
+
+    path = tmp_path / "ok.hbf"
+    _write(str(path), np.random.default_rng(2), nx=8, ny=8, leaf_pts=16, Lv=2, n_I=2)
+    data = path.read_bytes()
+
+    def load(blob):
+        p = tmp_path / "x.hbf"
+        p.write_bytes(blob)
+        h = C.c_void_p()
+        st = L.hb_load(str(p).encode(), C.byref(h))
+        if st == binding.HB_OK:
+            L.hb_destroy(h)
+        return st
+
+    expect_ok = binding.HB_OK if torch.cuda.is_available() else binding.HB_ERR_CUDA
+    assert load(data) == expect_ok
+    header = 8 + 8 * 14 + 8 * 2 * 2 + 8 * 3 * 16 + 8 * 64      # through n_cells
+    for cut in (0, 7, 8, 20, 100, header - 1):
+        assert load(data[:cut]) == binding.HB_ERR_ARG, cut
+    for cut in (header + 8, len(data) // 2, len(data) - 1):
+        assert load(data[:cut]) in (binding.HB_ERR_ARG, binding.HB_ERR_CUDA), cut
+    big = np.frombuffer(data, dtype=np.uint8).copy()
+    big[8:24] = np.frombuffer(np.array([1 << 31, 1 << 31], dtype="<i8").tobytes(), dtype=np.uint8)
+    assert load(big.tobytes()) == binding.HB_ERR_ARG        # N_v = 2^62 cells: refused by size
+    bad_magic = b"XBFACT01" + data[8:]
+    assert load(bad_magic) == binding.HB_ERR_ARG
