@@ -295,6 +295,19 @@ hb_status hb_id_batch_noalloc(int count, const int* m, const int* n, const long 
  * natural index, N_v int64) to a HOST array.  Valid after hb_create. */
 hb_status hb_tree_perm(hb_handle h, long long* perm_out);
 
+/* hb_host_cluster_tree / hb_host_proxy_rows: the host rules of hb_create and
+ * hb_build without a handle or a device, for an nx x ny grid: the K-D
+ * cluster tree (split the longer side of the node's bounding box in cells,
+ * order by (coordinate, natural index), first child ceil(n/2); L_v = the
+ * smallest L with ceil(N_v / 2^L) <= leaf; leaves in natural order) and the
+ * proxy rows of Eq. proxyv2v (as hb_proxy_rows, with chi and the neighbour
+ * radius in cells given here).  HOST arrays: perm_out N_v int64 (NULL to
+ * skip), bounds_out the node boundaries of levels 0..L_v concatenated
+ * (2^l + 1 per level; NULL to skip), *levels = L_v.  Errors: HB_ERR_ARG. */
+hb_status hb_host_cluster_tree(int nx, int ny, int leaf, long long* perm_out, long long* bounds_out, int* levels);
+hb_status hb_host_proxy_rows(int nx, int ny, int leaf, double chi, double nbr_radius_h, long long t0, long long t1,
+                             const long long* seeds, int nseeds, long long* out, long long* count);
+
 /* hb_proxy_rows: the proxy-row rule Eq. proxyv2v for the row node
  * tau = tree positions [t0, t1) and seed columns `seeds` (tree positions,
  * HOST).  Writes the sorted proxy tree positions to the HOST array out

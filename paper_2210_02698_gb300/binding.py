@@ -25,7 +25,7 @@ EXPORTS = ["hb_create", "hb_build", "hb_save", "hb_load", "hb_apply", "hb_apply_
            "hb_set_wait_selftest", "hb_device_alloc_cap",
            "hb_apply_dense", "hb_apply_dense_adjoint", "hb_entries", "hb_curve_set", "hb_curve_operators",
            "hb_apply_inclusion", "hb_id_batch", "hb_id_batch_noalloc",
-           "hb_tree_perm", "hb_proxy_rows", "hb_info", "hb_rank_profile", "hb_set_kernel_timing",
+           "hb_tree_perm", "hb_proxy_rows", "hb_host_cluster_tree", "hb_host_proxy_rows", "hb_info", "hb_rank_profile", "hb_set_kernel_timing",
            "hb_kernel_times", "hb_last_error", "hb_destroy"]
 
 
@@ -84,6 +84,8 @@ def lib():
         L.hb_proxy_rows.argtypes = [vp, ll, ll, vp, i, vp, vp]
         L.hb_info.argtypes = [vp, C.POINTER(Stats)]
         L.hb_rank_profile.argtypes = [vp, vp, vp]
+        L.hb_host_cluster_tree.argtypes = [i, i, i, vp, vp, C.POINTER(i)]
+        L.hb_host_proxy_rows.argtypes = [i, i, i, d, d, ll, ll, vp, i, vp, C.POINTER(ll)]
         L.hb_set_kernel_timing.argtypes = [vp, i]
         L.hb_kernel_times.argtypes = [vp, i, vp, vp, vp, vp]
         L.hb_last_error.argtypes = [vp]
@@ -288,6 +290,31 @@ class Operator:
         self._call("hb_kernel_times", cap, C.cast(names, C.c_void_p), C.cast(ms, C.c_void_p),
                    C.cast(cnt, C.c_void_p), C.byref(ng))
         return {bytes(names[i]).split(b"\0")[0].decode(): (ms[i], cnt[i]) for i in range(min(ng.value, cap))}
+
+
+def host_cluster_tree(nx, ny, leaf):
+    """hb_host_cluster_tree: (perm, [bounds of levels 0..L_v]) without a device."""
+    lv = C.c_int()
+    _check(lib().hb_host_cluster_tree(int(nx), int(ny), int(leaf), None, None, C.byref(lv)))
+    perm = np.empty(int(nx) * int(ny), dtype=np.int64)
+    bounds = np.empty(sum((1 << l) + 1 for l in range(lv.value + 1)), dtype=np.int64)
+    _check(lib().hb_host_cluster_tree(int(nx), int(ny), int(leaf), perm.ctypes.data, bounds.ctypes.data,
+                                      C.byref(lv)))
+    out, o = [], 0
+    for l in range(lv.value + 1):
+        out.append(bounds[o:o + (1 << l) + 1].copy())
+        o += (1 << l) + 1
+    return perm, out
+
+
+def host_proxy_rows(nx, ny, leaf, chi, radius, t0, t1, seeds):
+    """hb_host_proxy_rows: proxy tree positions of the row node [t0, t1)."""
+    seeds = np.ascontiguousarray(seeds, dtype=np.int64)
+    out = np.empty(max(int(t1) - int(t0), 1), dtype=np.int64)
+    cnt = C.c_longlong()
+    _check(lib().hb_host_proxy_rows(int(nx), int(ny), int(leaf), float(chi), float(radius), int(t0), int(t1),
+                                    seeds.ctypes.data, len(seeds), out.ctypes.data, C.byref(cnt)))
+    return out[:cnt.value].copy()
 
 
 def _id_args(A, m, n, a_off, rank, skel, V):

@@ -427,6 +427,54 @@ hb_status hb_proxy_rows(hb_handle h, long long t0, long long t1, const long long
   });
 }
 
+namespace {
+// A context holding only what the host rules read (no device state).
+void host_tree_ctx(hb_ctx& c, int nx, int ny, int leaf) {
+  if (nx < 1 || ny < 1 || (long long)nx * ny > (1LL << 31)) throw hb::arg_error("bad grid");
+  if (leaf < 1) throw hb::arg_error("leaf must be >= 1");
+  c.nx = nx;
+  c.ny = ny;
+  c.Nv = (long long)nx * ny;
+  c.opt.leaf = leaf;
+  hb::tree_build(&c);
+}
+}  // namespace
+
+hb_status hb_host_cluster_tree(int nx, int ny, int leaf, long long* perm_out, long long* bounds_out, int* levels) {
+  return guarded(nullptr, [&] {
+    if (!levels) throw hb::arg_error("null argument");
+    hb_ctx c;
+    host_tree_ctx(c, nx, ny, leaf);
+    *levels = c.Lv;
+    if (perm_out) std::memcpy(perm_out, c.perm.data(), sizeof(long long) * (size_t)c.Nv);
+    if (bounds_out)
+      for (int l = 0; l <= c.Lv; ++l) {
+        std::memcpy(bounds_out, c.bounds[(size_t)l].data(), sizeof(long long) * c.bounds[(size_t)l].size());
+        bounds_out += c.bounds[(size_t)l].size();
+      }
+  });
+}
+
+hb_status hb_host_proxy_rows(int nx, int ny, int leaf, double chi, double nbr_radius_h, long long t0, long long t1,
+                             const long long* seeds, int nseeds, long long* out, long long* count) {
+  return guarded(nullptr, [&] {
+    if (!out || !count || nseeds < 0 || (nseeds > 0 && !seeds)) throw hb::arg_error("null argument");
+    if (!(chi > 0) || !(nbr_radius_h >= 0)) throw hb::arg_error("bad options (chi > 0, radius >= 0)");
+    hb_ctx c;
+    c.opt.chi = chi;
+    c.opt.nbr_radius_h = nbr_radius_h;
+    host_tree_ctx(c, nx, ny, leaf);
+    if (t0 < 0 || t1 > c.Nv || t0 >= t1) throw hb::arg_error("bad range");
+    for (int s = 0; s < nseeds; ++s)
+      if (seeds[s] < 0 || seeds[s] >= c.Nv) throw hb::arg_error("seed out of range");
+    std::vector<long long> rows;
+    std::vector<int> stamp((size_t)c.Nv, -1);
+    hb::proxy_rows(&c, t0, t1, seeds, nseeds, rows, stamp, 1);
+    std::memcpy(out, rows.data(), sizeof(long long) * rows.size());
+    *count = (long long)rows.size();
+  });
+}
+
 hb_status hb_info(hb_handle h, hb_stats* stats) {
   return guarded(h, [&] {
     if (!h || !stats) throw hb::arg_error("null argument");

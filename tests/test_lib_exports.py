@@ -187,3 +187,41 @@ def test_factor_file_reader_rejects_corrupt_files_without_a_device(L, tmp_path):
     assert load(big.tobytes()) == binding.HB_ERR_ARG        # N_v = 2^62 cells: refused by size
     bad_magic = b"XBFACT01" + data[8:]
     assert load(bad_magic) == binding.HB_ERR_ARG
+
+
+@pytest.mark.parametrize("N,leaf", [(32, 64), (24, 20), (64, 64), (37, 10), (9, 64), (256, 64)])
+def test_host_tree_and_proxy_rows_match_oracle(L, N, leaf):
+    """The library's cluster tree and proxy-row rule (host code of hb_create /
+    hb_build, Sec. 4.2 and Eq. proxyv2v) equal the oracle's bit for bit,
+    without a device."""
+    from oracle import tree
+    from paper_2210_02698_gb300 import binding
+    perm, bounds = binding.host_cluster_tree(N, N, leaf)
+    operm, obounds = tree.cluster_tree(N, leaf)
+    assert np.array_equal(perm, operm)
+    assert len(bounds) == len(obounds) and all(np.array_equal(a, b) for a, b in zip(bounds, obounds))
+    rng = np.random.default_rng(N + leaf)
+    for lvl in range(1, len(bounds)):
+        for _ in range(3):
+            k = int(rng.integers(0, (1 << lvl) - 1))
+            t0, t1 = int(bounds[lvl][k]), int(bounds[lvl][k + 1])
+            s0, s1 = int(bounds[lvl][k + 1]), int(bounds[lvl][k + 2])
+            if s1 <= s0 or t1 <= t0:
+                continue
+            seeds = rng.choice(np.arange(s0, s1), size=min(s1 - s0, int(rng.integers(1, 9))), replace=False)
+            for chi, radius in ((20.0, 10.0), (2.0, 3.5)):
+                want = tree.proxy_rows(t0, t1, seeds, chi, radius, operm, N)
+                got = binding.host_proxy_rows(N, N, leaf, chi, radius, t0, t1, seeds)
+                assert np.array_equal(got, want), (lvl, k, chi, radius)
+
+
+def test_host_tree_on_rectangular_grids(L):
+    from paper_2210_02698_gb300 import binding
+    for nx, ny, leaf in ((40, 7, 16), (5, 33, 8), (1, 100, 7)):
+        perm, bounds = binding.host_cluster_tree(nx, ny, leaf)
+        assert sorted(perm.tolist()) == list(range(nx * ny))
+        assert bounds[-1][-1] == nx * ny and np.max(np.diff(bounds[-1])) <= leaf
+        for l in range(1, len(bounds)):
+            assert np.array_equal(bounds[l][::2], bounds[l - 1])
+    with pytest.raises(binding.HBError):
+        binding.host_cluster_tree(0, 5, 4)
