@@ -308,6 +308,16 @@ hb_status hb_host_cluster_tree(int nx, int ny, int leaf, long long* perm_out, lo
 hb_status hb_host_proxy_rows(int nx, int ny, int leaf, double chi, double nbr_radius_h, long long t0, long long t1,
                              const long long* seeds, int nseeds, long long* out, long long* count);
 
+/* hb_host_segment_tree: the K-D tree T_{H_s} over ns curve segment centres
+ * (centers: HOST ns x 2 (x, z) pairs) by the cluster tree's rule on real
+ * coordinates (split the longer side of the node's bounding box, order by
+ * (coordinate, segment index), first child ceil(n/2); leaves in index
+ * order), the column tree of the compressed surface operators (Sec. 4.2,
+ * the K^{s2v} and K^{s2s} items).  Outputs as hb_host_cluster_tree.
+ * Errors: HB_ERR_ARG. */
+hb_status hb_host_segment_tree(const double* centers, long long ns, int leaf, long long* perm_out,
+                               long long* bounds_out, int* levels);
+
 /* hb_proxy_rows: the proxy-row rule Eq. proxyv2v for the row node
  * tau = tree positions [t0, t1) and seed columns `seeds` (tree positions,
  * HOST).  Writes the sorted proxy tree positions to the HOST array out

@@ -25,7 +25,7 @@ EXPORTS = ["hb_create", "hb_build", "hb_save", "hb_load", "hb_apply", "hb_apply_
            "hb_set_wait_selftest", "hb_device_alloc_cap",
            "hb_apply_dense", "hb_apply_dense_adjoint", "hb_entries", "hb_curve_set", "hb_curve_operators",
            "hb_apply_inclusion", "hb_id_batch", "hb_id_batch_noalloc",
-           "hb_tree_perm", "hb_proxy_rows", "hb_host_cluster_tree", "hb_host_proxy_rows", "hb_info", "hb_rank_profile", "hb_set_kernel_timing",
+           "hb_tree_perm", "hb_proxy_rows", "hb_host_cluster_tree", "hb_host_proxy_rows", "hb_host_segment_tree", "hb_info", "hb_rank_profile", "hb_set_kernel_timing",
            "hb_kernel_times", "hb_last_error", "hb_destroy"]
 
 
@@ -86,6 +86,7 @@ def lib():
         L.hb_rank_profile.argtypes = [vp, vp, vp]
         L.hb_host_cluster_tree.argtypes = [i, i, i, vp, vp, C.POINTER(i)]
         L.hb_host_proxy_rows.argtypes = [i, i, i, d, d, ll, ll, vp, i, vp, C.POINTER(ll)]
+        L.hb_host_segment_tree.argtypes = [vp, ll, i, vp, vp, C.POINTER(i)]
         L.hb_set_kernel_timing.argtypes = [vp, i]
         L.hb_kernel_times.argtypes = [vp, i, vp, vp, vp, vp]
         L.hb_last_error.argtypes = [vp]
@@ -299,6 +300,22 @@ def host_cluster_tree(nx, ny, leaf):
     perm = np.empty(int(nx) * int(ny), dtype=np.int64)
     bounds = np.empty(sum((1 << l) + 1 for l in range(lv.value + 1)), dtype=np.int64)
     _check(lib().hb_host_cluster_tree(int(nx), int(ny), int(leaf), perm.ctypes.data, bounds.ctypes.data,
+                                      C.byref(lv)))
+    out, o = [], 0
+    for l in range(lv.value + 1):
+        out.append(bounds[o:o + (1 << l) + 1].copy())
+        o += (1 << l) + 1
+    return perm, out
+
+
+def host_segment_tree(centers, leaf):
+    """hb_host_segment_tree: (perm, [bounds of levels 0..L_s]) of the segment K-D tree."""
+    c = np.ascontiguousarray(centers, dtype=np.float64).reshape(-1, 2)
+    lv = C.c_int()
+    _check(lib().hb_host_segment_tree(c.ctypes.data, len(c), int(leaf), None, None, C.byref(lv)))
+    perm = np.empty(len(c), dtype=np.int64)
+    bounds = np.empty(sum((1 << l) + 1 for l in range(lv.value + 1)), dtype=np.int64)
+    _check(lib().hb_host_segment_tree(c.ctypes.data, len(c), int(leaf), perm.ctypes.data, bounds.ctypes.data,
                                       C.byref(lv)))
     out, o = [], 0
     for l in range(lv.value + 1):

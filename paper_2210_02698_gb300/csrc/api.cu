@@ -455,6 +455,32 @@ hb_status hb_host_cluster_tree(int nx, int ny, int leaf, long long* perm_out, lo
   });
 }
 
+hb_status hb_host_segment_tree(const double* centers, long long ns, int leaf, long long* perm_out,
+                               long long* bounds_out, int* levels) {
+  return guarded(nullptr, [&] {
+    if (!centers || !levels) throw hb::arg_error("null argument");
+    if (ns < 1 || ns > (1LL << 31)) throw hb::arg_error("segments outside [1, 2^31]");
+    if (leaf < 1) throw hb::arg_error("leaf must be >= 1");
+    std::vector<double> cx((size_t)ns), cz((size_t)ns);
+    for (long long i = 0; i < ns; ++i) {
+      cx[(size_t)i] = centers[2 * i];
+      cz[(size_t)i] = centers[2 * i + 1];
+      if (!std::isfinite(cx[(size_t)i]) || !std::isfinite(cz[(size_t)i]))
+        throw hb::arg_error("segment %lld: centre not finite", i);
+    }
+    std::vector<long long> perm;
+    std::vector<std::vector<long long>> bounds;
+    hb::segment_tree_build(cx.data(), cz.data(), ns, leaf, perm, bounds);
+    *levels = (int)bounds.size() - 1;
+    if (perm_out) std::memcpy(perm_out, perm.data(), sizeof(long long) * perm.size());
+    if (bounds_out)
+      for (const std::vector<long long>& b : bounds) {
+        std::memcpy(bounds_out, b.data(), sizeof(long long) * b.size());
+        bounds_out += b.size();
+      }
+  });
+}
+
 hb_status hb_host_proxy_rows(int nx, int ny, int leaf, double chi, double nbr_radius_h, long long t0, long long t1,
                              const long long* seeds, int nseeds, long long* out, long long* count) {
   return guarded(nullptr, [&] {

@@ -304,6 +304,9 @@ void curve_free(hb_ctx* c);
 void curve_operators(hb_ctx* c, double2* k_s2s, double2* k_v2s, double2* k_s2v, cudaStream_t st);
 void apply_inclusion(hb_ctx* c, const double2* s, double2* u, int nrhs, int v2v_dense, cudaStream_t st);
 void tree_build(hb_ctx* c);
+// K-D tree over curve segment centres (same split rule on real coordinates)
+void segment_tree_build(const double* cx, const double* cz, long long ns, int leaf, std::vector<long long>& perm,
+                        std::vector<std::vector<long long>>& bounds);
 void proxy_rows(const hb_ctx* c, long long t0, long long t1, const long long* seeds, int nseeds,
                 std::vector<long long>& out, std::vector<int>& stamp, int stamp_id);
 }  // namespace hb

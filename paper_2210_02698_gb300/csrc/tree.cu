@@ -68,6 +68,51 @@ void tree_build(hb_ctx* c) {
   for (long long i = 0; i < Nv; ++i) c->iperm[P[i]] = i;
 }
 
+void segment_tree_build(const double* cx, const double* cz, long long ns, int leaf, std::vector<long long>& perm,
+                        std::vector<std::vector<long long>>& bounds) {
+  int L = 0;
+  while ((ns + (1LL << L) - 1) / (1LL << L) > leaf) ++L;
+  std::vector<std::vector<long long>> nodes(1);
+  nodes[0].resize((size_t)ns);
+  std::iota(nodes[0].begin(), nodes[0].end(), 0LL);
+  bounds.assign(1, {0, ns});
+  std::vector<std::pair<double, long long>> keyed;
+  for (int l = 0; l < L; ++l) {
+    std::vector<std::vector<long long>> nxt;
+    nxt.reserve(nodes.size() * 2);
+    std::vector<long long> nb{0};
+    for (const std::vector<long long>& P : nodes) {
+      std::vector<long long> a, b;
+      if (!P.empty()) {
+        double xmin = cx[P[0]], xmax = xmin, zmin = cz[P[0]], zmax = zmin;
+        for (long long i : P) {
+          xmin = std::min(xmin, cx[i]);
+          xmax = std::max(xmax, cx[i]);
+          zmin = std::min(zmin, cz[i]);
+          zmax = std::max(zmax, cz[i]);
+        }
+        const bool splitx = (xmax - xmin) >= (zmax - zmin);
+        keyed.resize(P.size());
+        for (size_t i = 0; i < P.size(); ++i) keyed[i] = {splitx ? cx[P[i]] : cz[P[i]], P[i]};
+        std::sort(keyed.begin(), keyed.end());
+        const size_t n1 = (P.size() + 1) / 2;
+        for (size_t i = 0; i < keyed.size(); ++i) (i < n1 ? a : b).push_back(keyed[i].second);
+      }
+      nb.push_back(nb.back() + (long long)a.size());
+      nb.push_back(nb.back() + (long long)b.size());
+      nxt.push_back(std::move(a));
+      nxt.push_back(std::move(b));
+    }
+    nodes = std::move(nxt);
+    bounds.push_back(std::move(nb));
+  }
+  perm.clear();
+  for (std::vector<long long>& P : nodes) {
+    std::sort(P.begin(), P.end());
+    perm.insert(perm.end(), P.begin(), P.end());
+  }
+}
+
 void proxy_rows(const hb_ctx* c, long long t0, long long t1, const long long* seeds, int nseeds,
                 std::vector<long long>& out, std::vector<int>& stamp, int stamp_id) {
   out.clear();

@@ -225,3 +225,22 @@ def test_host_tree_on_rectangular_grids(L):
             assert np.array_equal(bounds[l][::2], bounds[l - 1])
     with pytest.raises(binding.HBError):
         binding.host_cluster_tree(0, 5, 4)
+
+
+def test_host_segment_tree_matches_oracle(L):
+    """The library's segment K-D tree (the column tree of the compressed
+    surface operators) equals the oracle prototype's bit for bit: a circle,
+    an open square (equal coordinates along its sides) and random points
+    with repeated coordinates (ties broken by segment index)."""
+    from oracle import curve_butterfly, inclusion
+    from paper_2210_02698_gb300 import binding, workloads as W
+    rng = np.random.default_rng(12)
+    sets = [W.circle_segments((0.5, 0.5), 0.3, 1000)[0],
+            inclusion.polyline([(0.1, 0.1), (0.1, 0.9), (0.9, 0.9), (0.9, 0.1)], 333).c,
+            np.round(rng.uniform(0, 1, size=(517, 2)), 1)]
+    for cen in sets:
+        for leaf in (1, 4, 37):
+            perm, bounds = binding.host_segment_tree(cen, leaf)
+            operm, obounds = curve_butterfly.segment_tree(cen, leaf)
+            assert np.array_equal(perm, operm)
+            assert len(bounds) == len(obounds) and all(np.array_equal(a, b) for a, b in zip(bounds, obounds))
