@@ -203,12 +203,24 @@ static inline int on_edge(int i, int j, int M) {
   return i < EDGE || j < EDGE || i >= M - EDGE || j >= M - EDGE;
 }
 
-/* visit the mesh in sweep order o (0..3) */
-#define SWEEP_BEGIN(o, M)                                            \
-  for (int jj = 0; jj < (M); ++jj) {                                 \
-    const int j = ((o) & 2) ? (M) - 1 - jj : jj;                     \
-    for (int ii = 0; ii < (M); ++ii) {                               \
-      const int i = (((o) == 1) || ((o) == 2)) ? (M) - 1 - ii : ii;  \
+/* Visit the mesh in sweep order o (0..3).  Rows one after the other
+ * (lexicographic Gauss-Seidel, the default), or anti-diagonals ii + jj = dd
+ * one after the other (g_wavefront != 0).  An update reads its row and its
+ * column only, so the points of one anti-diagonal never read each other and
+ * may be updated in any order (the order a parallel sweep takes); and along
+ * every row and column both orders visit the points in the same upwind
+ * order, so each update sees the same new and old values: the two orders
+ * compute the same iterates bit for bit. */
+static int g_wavefront = 0;
+
+#define SWEEP_BEGIN(o, M)                                                          \
+  for (int dd = 0; dd < (g_wavefront ? 2 * (M) - 1 : (M)); ++dd) {                 \
+    const int ilo = g_wavefront ? (dd - (M) + 1 > 0 ? dd - (M) + 1 : 0) : 0;       \
+    const int ihi = g_wavefront ? (dd < (M) - 1 ? dd : (M) - 1) : (M) - 1;         \
+    for (int ii = ilo; ii <= ihi; ++ii) {                                          \
+      const int jj = g_wavefront ? dd - ii : dd;                                   \
+      const int j = ((o) & 2) ? (M) - 1 - jj : jj;                                 \
+      const int i = (((o) == 1) || ((o) == 2)) ? (M) - 1 - ii : ii;                \
       const size_t p = (size_t)j * (M) + i;
 #define SWEEP_END \
   }               \
@@ -427,6 +439,19 @@ static int check_mesh(int M, double h, int w0, int w1, int roi0, int roi1) {
  * ns x TAYLOR_LEN; n_mesh is n on the mesh (M x M).  info: ns x 6
  * (iterations and last updates of the three solves).  Returns 0, or -1 on
  * a bad argument or when out of memory. */
+/* 0: row-by-row sweeps (default); 1: anti-diagonal (wavefront) sweeps.
+ * Set before a call, not during one. */
+void hb_oracle_sweep_set_order(int wavefront) { g_wavefront = wavefront != 0; }
+
+/* The visiting order of sweep o on an M x M mesh under the current order
+ * setting: out[k] = the k-th point visited (j M + i). */
+void hb_oracle_sweep_visit_order(int o, int M, long long* out) {
+  long long k = 0;
+  SWEEP_BEGIN(o, M)
+  out[k++] = (long long)p;
+  SWEEP_END
+}
+
 int hb_oracle_sweep_tables(int M, double lo, double h, int w0, int w1, int roi0, int roi1, const double* n_mesh,
                            int NI, const double* px, const double* pz, int ns, const int* src, const double* taylor,
                            int max_iter, double tol, double* tau2, double* v0, double* v1, double* info) {

@@ -66,6 +66,10 @@ def lib():
         L.hb_oracle_sweep_tables.restype = ctypes.c_int
         L.hb_oracle_sweep_fields.argtypes = [ci, cd, cd, ci, ci, ci, ci, dp, cd, cd, dp, ci, cd, dp, dp, dp, dp]
         L.hb_oracle_sweep_fields.restype = ctypes.c_int
+        L.hb_oracle_sweep_set_order.argtypes = [ci]
+        L.hb_oracle_sweep_set_order.restype = None
+        L.hb_oracle_sweep_visit_order.argtypes = [ci, ci, ctypes.POINTER(ctypes.c_longlong)]
+        L.hb_oracle_sweep_visit_order.restype = None
         _lib = L
     return _lib
 
@@ -144,10 +148,33 @@ def mesh_n(medium, M, lo, h0):
     return np.ascontiguousarray(medium.n(X, Z), dtype=np.float64), X, Z
 
 
-def fields(medium, x0, z0, h0, margin=0.3, max_iter=500, tol=1e-12):
+class _Order:
+    """Sweep order of the calls inside the block: rows (default) or
+    anti-diagonals (``wavefront``), restored to rows on exit."""
+
+    def __init__(self, wavefront):
+        self.wavefront = wavefront
+
+    def __enter__(self):
+        lib().hb_oracle_sweep_set_order(1 if self.wavefront else 0)
+
+    def __exit__(self, *exc):
+        lib().hb_oracle_sweep_set_order(0)
+
+
+def visit_order(o, M, wavefront=False):
+    """The points (j M + i) in the order sweep o visits them."""
+    out = np.empty(M * M, dtype=np.int64)
+    with _Order(wavefront):
+        lib().hb_oracle_sweep_visit_order(o, M, out.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)))
+    return out
+
+
+def fields(medium, x0, z0, h0, margin=0.3, max_iter=500, tol=1e-12, wavefront=False):
     """Mesh fields of one source: tau^2, v0, v1 (each [j][i] on the mesh;
     v0 and v1 are NaN outside the transport window), the mesh coordinates
-    and (iterations, last update) of the three solves."""
+    and (iterations, last update) of the three solves.  ``wavefront``: sweep
+    anti-diagonal by anti-diagonal instead of row by row (same fixed point)."""
     M, lo, w0, w1, roi0, roi1 = mesh(h0, margin)
     n, X, Z = mesh_n(medium, M, lo, h0)
     tin = taylor_input(medium, x0, z0)
@@ -156,8 +183,9 @@ def fields(medium, x0, z0, h0, margin=0.3, max_iter=500, tol=1e-12):
     a0 = np.empty((Mw, Mw))
     a1 = np.empty((Mw, Mw))
     info = np.empty(6)
-    r = lib().hb_oracle_sweep_fields(M, lo, h0, w0, w1, roi0, roi1, _p(n), x0, z0, _p(tin), max_iter, tol, _p(t2),
-                                     _p(a0), _p(a1), _p(info))
+    with _Order(wavefront):
+        r = lib().hb_oracle_sweep_fields(M, lo, h0, w0, w1, roi0, roi1, _p(n), x0, z0, _p(tin), max_iter, tol,
+                                         _p(t2), _p(a0), _p(a1), _p(info))
     if r != 0:
         raise RuntimeError("sweep failed")
     v0 = np.full((M, M), np.nan)
