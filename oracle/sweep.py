@@ -37,17 +37,23 @@ TAYLOR_LEN = 46
 _lib = None
 
 
+# -ffp-contract=off: every a*b + c rounds twice, as written, on every
+# architecture (GCC contracts it into one fused multiply-add by default where
+# the hardware has one), so the oracle's results are the same on x86 and Arm
+CFLAGS = ["-std=c99", "-O2", "-ffp-contract=off", "-fPIC", "-shared"]
+
+
 def compile_library():
-    """gcc -O2 -fPIC -shared [-fopenmp] oracle/sweep.c; cached by source hash."""
+    """gcc CFLAGS [-fopenmp] oracle/sweep.c; cached by source and flags."""
     with open(SRC, "rb") as f:
-        tag = hashlib.sha256(f.read()).hexdigest()[:12]
+        tag = hashlib.sha256(f.read() + " ".join(CFLAGS).encode()).hexdigest()[:12]
     out = os.path.join(BUILD, f"libhbsweep_{tag}.so")
     if os.path.exists(out):
         return out
     os.makedirs(BUILD, exist_ok=True)
     tmp = out + f".{os.getpid()}.tmp"
-    base = ["gcc", "-std=c99", "-O2", "-fPIC", "-shared", SRC, "-o", tmp, "-lm"]
-    r = subprocess.run(base[:5] + ["-fopenmp"] + base[5:], capture_output=True, text=True)
+    base = ["gcc", *CFLAGS, SRC, "-o", tmp, "-lm"]
+    r = subprocess.run(base[:len(CFLAGS) + 1] + ["-fopenmp"] + base[len(CFLAGS) + 1:], capture_output=True, text=True)
     if r.returncode != 0:
         subprocess.run(base, check=True, capture_output=True, text=True)
     os.replace(tmp, out)

@@ -166,7 +166,8 @@ def test_lens_tables_match_ray_tracing():
 def test_stored_lens_tables_are_the_builders_output():
     """Provenance of the stored lens tables: one column regenerated by the
     committed builder at the stored mesh (h0 = 1/256) reproduces them (to
-    rounding: contraction of multiply-adds may differ between compilers)."""
+    rounding: the builder is compiled without contracted multiply-adds, but
+    libm's exp, pow and cos may differ between platforms)."""
     t, _ = _lens()
     j = 137
     r = sweep.build_tables(W.LENS, 16, h0=1 / 256, sources=[j])
