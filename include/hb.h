@@ -318,6 +318,17 @@ hb_status hb_host_proxy_rows(int nx, int ny, int leaf, double chi, double nbr_ra
 hb_status hb_host_segment_tree(const double* centers, long long ns, int leaf, long long* perm_out,
                                long long* bounds_out, int* levels);
 
+/* hb_host_point_proxy_rows: Eq. proxyv2v between two point sets, the rule of
+ * the compressed surface operators (rows: cells or segment centres in tree
+ * order; seeds: points of the other set): m = min(t1 - t0, ceil(chi nseeds))
+ * rows of [t0, t1) at positions t0 + floor(k (t1 - t0) / m), plus every row
+ * of [t0, t1) within `radius` (domain units) of a seed.  rows_xz: HOST
+ * nrows x 2, seeds_xz: HOST nseeds x 2; out: HOST, capacity t1 - t0, sorted
+ * positions; *count their number.  Errors: HB_ERR_ARG. */
+hb_status hb_host_point_proxy_rows(const double* rows_xz, long long nrows, long long t0, long long t1,
+                                   const double* seeds_xz, int nseeds, double chi, double radius, long long* out,
+                                   long long* count);
+
 /* hb_proxy_rows: the proxy-row rule Eq. proxyv2v for the row node
  * tau = tree positions [t0, t1) and seed columns `seeds` (tree positions,
  * HOST).  Writes the sorted proxy tree positions to the HOST array out

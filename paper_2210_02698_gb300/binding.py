@@ -25,7 +25,7 @@ EXPORTS = ["hb_create", "hb_build", "hb_save", "hb_load", "hb_apply", "hb_apply_
            "hb_set_wait_selftest", "hb_device_alloc_cap",
            "hb_apply_dense", "hb_apply_dense_adjoint", "hb_entries", "hb_curve_set", "hb_curve_operators",
            "hb_apply_inclusion", "hb_id_batch", "hb_id_batch_noalloc",
-           "hb_tree_perm", "hb_proxy_rows", "hb_host_cluster_tree", "hb_host_proxy_rows", "hb_host_segment_tree", "hb_info", "hb_rank_profile", "hb_set_kernel_timing",
+           "hb_tree_perm", "hb_proxy_rows", "hb_host_cluster_tree", "hb_host_proxy_rows", "hb_host_segment_tree", "hb_host_point_proxy_rows", "hb_info", "hb_rank_profile", "hb_set_kernel_timing",
            "hb_kernel_times", "hb_last_error", "hb_destroy"]
 
 
@@ -87,6 +87,7 @@ def lib():
         L.hb_host_cluster_tree.argtypes = [i, i, i, vp, vp, C.POINTER(i)]
         L.hb_host_proxy_rows.argtypes = [i, i, i, d, d, ll, ll, vp, i, vp, C.POINTER(ll)]
         L.hb_host_segment_tree.argtypes = [vp, ll, i, vp, vp, C.POINTER(i)]
+        L.hb_host_point_proxy_rows.argtypes = [vp, ll, ll, ll, vp, i, d, d, vp, C.POINTER(ll)]
         L.hb_set_kernel_timing.argtypes = [vp, i]
         L.hb_kernel_times.argtypes = [vp, i, vp, vp, vp, vp]
         L.hb_last_error.argtypes = [vp]
@@ -322,6 +323,17 @@ def host_segment_tree(centers, leaf):
         out.append(bounds[o:o + (1 << l) + 1].copy())
         o += (1 << l) + 1
     return perm, out
+
+
+def host_point_proxy_rows(rows_xz, t0, t1, seeds_xz, chi, radius):
+    """hb_host_point_proxy_rows: proxy positions of rows [t0, t1) for seed points."""
+    r = np.ascontiguousarray(rows_xz, dtype=np.float64).reshape(-1, 2)
+    sd = np.ascontiguousarray(seeds_xz, dtype=np.float64).reshape(-1, 2)
+    out = np.empty(max(int(t1) - int(t0), 1), dtype=np.int64)
+    cnt = C.c_longlong()
+    _check(lib().hb_host_point_proxy_rows(r.ctypes.data, len(r), int(t0), int(t1), sd.ctypes.data, len(sd),
+                                          float(chi), float(radius), out.ctypes.data, C.byref(cnt)))
+    return out[:cnt.value].copy()
 
 
 def host_proxy_rows(nx, ny, leaf, chi, radius, t0, t1, seeds):

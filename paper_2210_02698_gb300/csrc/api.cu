@@ -481,6 +481,20 @@ hb_status hb_host_segment_tree(const double* centers, long long ns, int leaf, lo
   });
 }
 
+hb_status hb_host_point_proxy_rows(const double* rows_xz, long long nrows, long long t0, long long t1,
+                                   const double* seeds_xz, int nseeds, double chi, double radius, long long* out,
+                                   long long* count) {
+  return guarded(nullptr, [&] {
+    if (!rows_xz || !out || !count || nseeds < 0 || (nseeds > 0 && !seeds_xz)) throw hb::arg_error("null argument");
+    if (t0 < 0 || t1 > nrows || t0 >= t1) throw hb::arg_error("bad range");
+    if (!(chi > 0) || !(radius >= 0)) throw hb::arg_error("bad options (chi > 0, radius >= 0)");
+    std::vector<long long> rows;
+    hb::point_proxy_rows(rows_xz, t0, t1, seeds_xz, nseeds, chi, radius, rows);
+    std::memcpy(out, rows.data(), sizeof(long long) * rows.size());
+    *count = (long long)rows.size();
+  });
+}
+
 hb_status hb_host_proxy_rows(int nx, int ny, int leaf, double chi, double nbr_radius_h, long long t0, long long t1,
                              const long long* seeds, int nseeds, long long* out, long long* count) {
   return guarded(nullptr, [&] {

@@ -307,6 +307,9 @@ void tree_build(hb_ctx* c);
 // K-D tree over curve segment centres (same split rule on real coordinates)
 void segment_tree_build(const double* cx, const double* cz, long long ns, int leaf, std::vector<long long>& perm,
                         std::vector<std::vector<long long>>& bounds);
+// Eq. proxyv2v between two point sets (rows and seed columns in real coordinates)
+void point_proxy_rows(const double* rows_xz, long long t0, long long t1, const double* seeds_xz, int nseeds,
+                      double chi, double radius, std::vector<long long>& out);
 void proxy_rows(const hb_ctx* c, long long t0, long long t1, const long long* seeds, int nseeds,
                 std::vector<long long>& out, std::vector<int>& stamp, int stamp_id);
 }  // namespace hb

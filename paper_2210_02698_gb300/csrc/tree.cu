@@ -113,6 +113,32 @@ void segment_tree_build(const double* cx, const double* cz, long long ns, int le
   }
 }
 
+void point_proxy_rows(const double* rows_xz, long long t0, long long t1, const double* seeds_xz, int nseeds,
+                      double chi, double radius, std::vector<long long>& out) {
+  out.clear();
+  const long long size = t1 - t0;
+  const long long m = std::min(size, (long long)std::ceil(chi * (double)nseeds));
+  if (m >= size) {
+    out.resize((size_t)size);
+    std::iota(out.begin(), out.end(), t0);
+    return;
+  }
+  for (long long k = 0; k < m; ++k) out.push_back(t0 + (k * size) / m);
+  const double R2 = radius * radius;
+  for (long long pos = t0; pos < t1; ++pos) {
+    const double x = rows_xz[2 * pos], z = rows_xz[2 * pos + 1];
+    for (int s = 0; s < nseeds; ++s) {
+      const double dx = x - seeds_xz[2 * s], dz = z - seeds_xz[2 * s + 1];
+      if (dx * dx + dz * dz <= R2) {
+        out.push_back(pos);
+        break;
+      }
+    }
+  }
+  std::sort(out.begin(), out.end());
+  out.erase(std::unique(out.begin(), out.end()), out.end());
+}
+
 void proxy_rows(const hb_ctx* c, long long t0, long long t1, const long long* seeds, int nseeds,
                 std::vector<long long>& out, std::vector<int>& stamp, int stamp_id) {
   out.clear();

@@ -244,3 +244,32 @@ def test_host_segment_tree_matches_oracle(L):
             operm, obounds = curve_butterfly.segment_tree(cen, leaf)
             assert np.array_equal(perm, operm)
             assert len(bounds) == len(obounds) and all(np.array_equal(a, b) for a, b in zip(bounds, obounds))
+
+
+def test_host_point_proxy_rows_match_oracle_prototype(L):
+    """The native two-set proxy rule equals the compressed-inclusion
+    prototype's (oracle/curve_butterfly.py) bit for bit: cells as rows with
+    segment centres as seeds, and segments as rows with cells as seeds."""
+    from types import SimpleNamespace
+    from oracle import curve_butterfly as cb, tree
+    from paper_2210_02698_gb300 import binding, workloads as W
+    N = 32
+    g = W.Grid(N)
+    x, z = g.centroids()
+    vperm, vb = tree.cluster_tree(N, 16)
+    cells = np.stack([x, z], axis=1)[vperm]
+    cen, _ = W.circle_segments((0.5, 0.5), 0.25, 256)
+    sperm, sb = cb.segment_tree(cen, 4)
+    segs = cen[sperm]
+    rng = np.random.default_rng(5)
+    for rows, cols, rb, cbounds in ((cells, segs, vb, sb), (segs, cells, sb, vb)):
+        for chi, radius in ((20.0, 10.0 / N), (1.5, 3.0 / N), (0.5, 0.0)):
+            obj = SimpleNamespace(chi=chi, radius=radius, rows=SimpleNamespace(pts=rows),
+                                  cols=SimpleNamespace(pts=cols))
+            for lvl in (1, 3, 5):
+                k = int(rng.integers(0, 1 << lvl))
+                t0, t1 = int(rb[lvl][k]), int(rb[lvl][k + 1])
+                seeds = rng.choice(len(cols), size=int(rng.integers(1, 6)), replace=False)
+                want = cb.Butterfly._proxy(obj, t0, t1, seeds)
+                got = binding.host_point_proxy_rows(rows, t0, t1, cols[seeds], chi, radius)
+                assert np.array_equal(got, want), (lvl, chi, radius)
