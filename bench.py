@@ -3,8 +3,9 @@
 Workload: 2D constant-gradient velocity c = 1 + 0.5 z on the unit square,
 256 x 256 cells (N_v = 65536), omega = 2 pi * 32, n_I = 16 Chebyshev tables,
 HODBF / butterfly compression at eps = 1e-6, 16 seeded complex Gaussian
-right-hand sides, mixed precision (FP32 factors, split-BF16 tensor-core
-products, FP32 accumulation).  One step = one hb_apply: gather + scale into
+right-hand sides, mixed precision (factors and vectors as split-BF16 pairs,
+three BF16 tensor-core products per complex multiply-add, FP32
+accumulation).  One step = one hb_apply: gather + scale into
 tree order, every butterfly level of every HODBF block, dense leaves,
 scatter back - the whole hot path of the apply.  The factors (hundreds of MB)
 exceed the 129 MB L2, so no flush is needed between steps.

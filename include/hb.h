@@ -10,8 +10,9 @@
  * (Sec. 4.1, Eq. chebinterp) and K_ii is the cell-integrated self term of
  * Appendix A (Eq. HankelIntegral2dlemma) divided by h^2.  The operator is
  * applied densely (matrix free, FP64) or in HODBF / butterfly-compressed form
- * (Sec. 4.2, Eq. butterfly_mat), in FP64 or with FP32 factors and split-BF16
- * tensor-core products accumulated in FP32.
+ * (Sec. 4.2, Eq. butterfly_mat), in FP64 or with factors and vectors stored as
+ * split-BF16 pairs (hi + lo) and three BF16 tensor-core products per complex
+ * multiply-add, accumulated in FP32.
  *
  * Conventions shared by every entry point:
  *  - Cells are in natural order: index = b*nx + a, a the x index (fastest),
@@ -280,8 +281,12 @@ hb_status hb_id_batch(int count, const int* m, const int* n, const long long* a_
  * static device array that every GPU loading the library keeps until the
  * process exits.  Limit: count <= 65536 matrices (larger counts return
  * HB_ERR_ARG with a message; nothing is launched).
- * Asynchronous on `stream` (NULL = legacy default stream); the host arrays
- * m, n, a_off may be reused on return.  The first call on a device looks up
+ * Asynchronous on `stream` (NULL = legacy default stream).  The host arrays
+ * m, n, a_off, pageable or page-locked, may be reused or freed on return:
+ * the call copies them into a static host array (pageable memory) before it
+ * enqueues the host-to-device copy, which has then consumed its source.
+ * Host threads calling this entry point serialise on a mutex for the
+ * duration of the call's enqueueing.  The first call on a device looks up
  * the array's device address (cudaGetSymbolAddress) for that device: make
  * that first call before any stream capture.  All calls share the array,
  * whose contents after a call are that call's metadata; each call writes
@@ -290,6 +295,26 @@ hb_status hb_id_batch(int count, const int* m, const int* n, const long long* a_
  * synchronisation in between) race on it. */
 hb_status hb_id_batch_noalloc(int count, const int* m, const int* n, const long long* a_off,
                               void* A, double eps, int* rank, int* skel, void* V, void* stream);
+
+/* hb_record_id_blocks / hb_recorded_id_count / hb_recorded_id_block: keep,
+ * for a check of the interpolative decomposition (Sec. 4.2.1, Eq. ID, on the
+ * blocks of Eq. proxy), copies of the sampled blocks that hb_build hands to
+ * its ID.  Call hb_record_id_blocks before hb_build (HB_ERR_STATE after):
+ * at every butterfly level k the build then keeps up to per_level of that
+ * level's blocks, every (blocks / per_level)-th one in the build's job order
+ * (0 = keep none, the default).  Each kept record holds the level k, the
+ * proxy rows and the column set as natural indices (m and n of them), the
+ * sampled m x n block as the ID received it (complex128, column-major), the
+ * rank the ID chose and its full pivot order (n positions in the column
+ * set; the first rank of them are the skeleton).  hb_recorded_id_block
+ * copies record `index` into HOST arrays: level, m, n and rank always;
+ * rows (m), cols (n), A (m*n complex128) and pivots (n) unless NULL, so a
+ * first call with NULL arrays returns the sizes.  Records live until the
+ * handle is destroyed.  Errors: HB_ERR_ARG (index out of range). */
+hb_status hb_record_id_blocks(hb_handle h, int per_level);
+hb_status hb_recorded_id_count(hb_handle h, int* count);
+hb_status hb_recorded_id_block(hb_handle h, int index, int* level, int* m, int* n, long long* rows,
+                               long long* cols, void* A, int* rank, int* pivots);
 
 /* hb_tree_perm: copy the cluster-tree permutation (tree position ->
  * natural index, N_v int64) to a HOST array.  Valid after hb_create. */

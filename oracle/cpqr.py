@@ -8,14 +8,33 @@ relative tolerance, and V = [I | R11^-1 R12] Pi^T.
 
 Readings (the paper says only "rank-revealing QR with a relative tolerance"):
 * step k pivots on the trailing column of largest 2-norm, the norms
-  recomputed from the current trailing matrix (no downdating); exact ties go
-  to the lowest current column position;
+  recomputed from the current trailing matrix (no downdating); columns whose
+  norm comes within TIE |R_00| of the largest (within a factor 1 - TIE at
+  step 0) count as tied, and the lowest current position among them wins.
+  Blocks of a regular grid hold columns that are mirror images of one
+  another, whose norms agree in exact arithmetic and differ only by rounding;
+  with the window, two implementations that round differently still pick the
+  same pivot (a difference in the last bits of a norm changes nothing unless
+  it straddles the window's edge);
 * the rank is the first k >= 1 with |R_kk| <= eps |R_00| (k = min(m, n) if
   none); an all-zero matrix gets rank 1;
 * the skeleton list is in pivot order.
 """
 import numpy as np
 from scipy.linalg import solve_triangular
+
+
+TIE = 1e-12   # tie window, relative to |R_00|
+
+
+def pivot(norms, k, r00):
+    """Position (within the trailing columns) of the step-k pivot and the
+    largest trailing norm: the lowest position whose norm is at least the
+    largest minus TIE |R_00| (at step 0, r00 unknown: the largest times
+    1 - TIE)."""
+    top = float(np.max(norms))
+    thr = top * (1.0 - TIE) if k == 0 else top - TIE * r00
+    return int(np.nonzero(norms >= thr)[0][0]), top
 
 
 def cpqr_id(A, eps):
@@ -28,14 +47,15 @@ def cpqr_id(A, eps):
     r = kmax
     for k in range(kmax):
         norms = np.sqrt(np.sum(np.abs(A[k:, k:]) ** 2, axis=0))
-        p = k + int(np.argmax(norms))          # argmax returns the first maximum
+        q, top = pivot(norms, k, r00 if k else 0.0)
+        p = k + q
         if k == 0:
-            r00 = norms[p - k]
-            if r00 == 0.0:
+            r00 = norms[q]
+            if top == 0.0:
                 r = 1
                 rdiag.append(0.0)
                 break
-        elif norms[p - k] <= eps * r00:
+        elif top <= eps * r00:
             r = k
             break
         if p != k:

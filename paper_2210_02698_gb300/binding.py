@@ -25,6 +25,7 @@ EXPORTS = ["hb_create", "hb_build", "hb_save", "hb_load", "hb_apply", "hb_apply_
            "hb_set_wait_selftest", "hb_device_alloc_cap",
            "hb_apply_dense", "hb_apply_dense_adjoint", "hb_entries", "hb_curve_set", "hb_curve_operators",
            "hb_apply_inclusion", "hb_id_batch", "hb_id_batch_noalloc",
+           "hb_record_id_blocks", "hb_recorded_id_count", "hb_recorded_id_block",
            "hb_tree_perm", "hb_proxy_rows", "hb_host_cluster_tree", "hb_host_proxy_rows", "hb_host_segment_tree", "hb_host_point_proxy_rows", "hb_info", "hb_rank_profile", "hb_set_kernel_timing",
            "hb_kernel_times", "hb_last_error", "hb_destroy"]
 
@@ -80,6 +81,10 @@ def lib():
         L.hb_apply_inclusion.argtypes = [vp, vp, vp, i, i, vp]
         L.hb_id_batch.argtypes = [i, vp, vp, vp, vp, d, vp, vp, vp]
         L.hb_id_batch_noalloc.argtypes = [i, vp, vp, vp, vp, d, vp, vp, vp, vp]
+        L.hb_record_id_blocks.argtypes = [vp, i]
+        L.hb_recorded_id_count.argtypes = [vp, C.POINTER(i)]
+        L.hb_recorded_id_block.argtypes = [vp, i, C.POINTER(i), C.POINTER(i), C.POINTER(i), vp, vp, vp,
+                                           C.POINTER(i), vp]
         L.hb_tree_perm.argtypes = [vp, vp]
         L.hb_proxy_rows.argtypes = [vp, ll, ll, vp, i, vp, vp]
         L.hb_info.argtypes = [vp, C.POINTER(Stats)]
@@ -265,6 +270,32 @@ class Operator:
         self._call("hb_proxy_rows", int(t0), int(t1), seeds.ctypes.data, len(seeds), out.ctypes.data,
                    C.byref(cnt))
         return out[:cnt.value].copy()
+
+    def record_id_blocks(self, per_level):
+        """hb_record_id_blocks: before build(), keep up to per_level of the
+        sampled blocks the ID decomposes at every butterfly level."""
+        self._call("hb_record_id_blocks", int(per_level))
+
+    def recorded_id_blocks(self):
+        """The kept blocks (hb_recorded_id_block): a list of dicts with the
+        level, proxy rows and columns (natural indices), the sampled block A
+        (m x n complex128), the rank and the full pivot order."""
+        cnt = C.c_int()
+        self._call("hb_recorded_id_count", C.byref(cnt))
+        out = []
+        for q in range(cnt.value):
+            lv, m, n, r = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+            self._call("hb_recorded_id_block", q, C.byref(lv), C.byref(m), C.byref(n), None, None, None,
+                       C.byref(r), None)
+            rows = np.empty(m.value, dtype=np.int64)
+            cols = np.empty(n.value, dtype=np.int64)
+            A = np.empty((n.value, m.value), dtype=np.complex128)   # column-major m x n
+            piv = np.empty(n.value, dtype=np.int32)
+            self._call("hb_recorded_id_block", q, C.byref(lv), C.byref(m), C.byref(n), rows.ctypes.data,
+                       cols.ctypes.data, A.ctypes.data, C.byref(r), piv.ctypes.data)
+            out.append({"level": lv.value, "rows": rows, "cols": cols, "A": A.T.copy(), "rank": r.value,
+                        "pivots": piv})
+        return out
 
     def info(self):
         s = Stats()

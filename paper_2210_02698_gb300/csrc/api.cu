@@ -245,9 +245,45 @@ hb_status hb_build(hb_handle h) {
         hb::flow_plan_free(h->flow_plan[d]);
         h->flow_plan[d] = nullptr;
       }
+      h->id_recs.clear();
       throw;
     }
     h->built = true;
+  });
+}
+
+hb_status hb_record_id_blocks(hb_handle h, int per_level) {
+  return guarded(h, [&] {
+    if (!h) throw hb::arg_error("null handle");
+    if (per_level < 0) throw hb::arg_error("per_level must be >= 0");
+    if (h->built) throw hb::Error{HB_ERR_STATE, "hb_record_id_blocks must come before hb_build"};
+    h->id_rec_per_level = per_level;
+    h->id_recs.clear();
+  });
+}
+
+hb_status hb_recorded_id_count(hb_handle h, int* count) {
+  return guarded(h, [&] {
+    if (!h || !count) throw hb::arg_error("null argument");
+    *count = (int)h->id_recs.size();
+  });
+}
+
+hb_status hb_recorded_id_block(hb_handle h, int index, int* level, int* m, int* n, long long* rows,
+                               long long* cols, void* A, int* rank, int* pivots) {
+  return guarded(h, [&] {
+    if (!h || !level || !m || !n || !rank) throw hb::arg_error("null argument");
+    if (index < 0 || index >= (int)h->id_recs.size())
+      throw hb::arg_error("record %d out of range (%d kept)", index, (int)h->id_recs.size());
+    const hb::IdRecord& r = h->id_recs[(size_t)index];
+    *level = r.level;
+    *m = (int)r.rows.size();
+    *n = (int)r.cols.size();
+    *rank = r.rank;
+    if (rows) std::copy(r.rows.begin(), r.rows.end(), rows);
+    if (cols) std::copy(r.cols.begin(), r.cols.end(), cols);
+    if (A) std::copy(r.A.begin(), r.A.end(), static_cast<double2*>(A));
+    if (pivots) std::copy(r.piv.begin(), r.piv.end(), pivots);
   });
 }
 

@@ -146,6 +146,13 @@ void build(hb_ctx* c) {
       for (int i = 0; i < (1 << k); ++i)
         for (int j = 0; j < (1 << (b.L - k)); ++j) desc.push_back(Job{bi, k, i, j, {}, {}});
     }
+    // blocks of this level kept for hb_record_id_blocks: every step-th job
+    const size_t rec_step = c->id_rec_per_level > 0
+                                ? std::max<size_t>(1, desc.size() / (size_t)c->id_rec_per_level)
+                                : 0;
+    auto recorded = [&](size_t q) {
+      return rec_step && q % rec_step == 0 && q / rec_step < (size_t)c->id_rec_per_level;
+    };
     const size_t JC = 8192;
     for (size_t j0 = 0; j0 < desc.size(); j0 += JC) {
       const size_t j1 = std::min(desc.size(), j0 + JC);
@@ -181,11 +188,20 @@ void build(hb_ctx* c) {
         std::vector<long long> haoff(cnt), hsoff(cnt);
         long long aoff = 0, soff = 0;
         int max_n = 1;
+        std::vector<std::pair<int, size_t>> rec_here;   // (t, index in c->id_recs)
         for (int t = 0; t < cnt; ++t) {
           Job& jb = desc[q0 + t];
           std::vector<long long> rn(jb.rows.size()), cn(jb.cols.size());
           for (size_t a = 0; a < rn.size(); ++a) rn[a] = c->perm[jb.rows[a]];
           for (size_t a = 0; a < cn.size(); ++a) cn[a] = c->perm[jb.cols[a]];
+          if (recorded(q0 + t)) {
+            IdRecord rec;
+            rec.level = k;
+            rec.rows = rn;
+            rec.cols = cn;
+            rec_here.push_back({t, c->id_recs.size()});
+            c->id_recs.push_back(std::move(rec));
+          }
           add_block(B, c, rn.data(), (long long)rn.size(), cn.data(), (long long)cn.size(), aoff);
           hm[t] = (int)rn.size();
           hn[t] = (int)cn.size();
@@ -198,6 +214,12 @@ void build(hb_ctx* c) {
         sampled += aoff;
         id_blocks += cnt;
         run_blocks(c, B, d_A, st);
+        for (const auto& rh : rec_here) {   // the samples as the ID receives them
+          IdRecord& rec = c->id_recs[rh.second];
+          rec.A.resize((size_t)hm[rh.first] * hn[rh.first]);
+          HB_CUDA(cudaMemcpyAsync(rec.A.data(), d_A + haoff[rh.first], sizeof(double2) * rec.A.size(),
+                                  cudaMemcpyDeviceToHost, st));
+        }
         int* d_m = upload(hm);
         int* d_n = upload(hn);
         long long* d_aoff = upload(haoff);
@@ -209,6 +231,11 @@ void build(hb_ctx* c) {
         HB_CUDA(cudaMemcpyAsync(hrank.data(), d_rank, sizeof(int) * cnt, cudaMemcpyDeviceToHost, st));
         HB_CUDA(cudaMemcpyAsync(hperm.data(), d_perm, sizeof(int) * soff, cudaMemcpyDeviceToHost, st));
         HB_CUDA(cudaStreamSynchronize(st));
+        for (const auto& rh : rec_here) {
+          IdRecord& rec = c->id_recs[rh.second];
+          rec.rank = hrank[rh.first];
+          rec.piv.assign(hperm.begin() + hsoff[rh.first], hperm.begin() + hsoff[rh.first] + hn[rh.first]);
+        }
         std::vector<long long> hvoff(cnt);
         long long vacc = 0;
         for (int t = 0; t < cnt; ++t) {

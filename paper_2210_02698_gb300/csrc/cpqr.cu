@@ -5,7 +5,10 @@
 // skel) V with skel the first r pivots and V = [I | R11^-1 R12] P^T:
 //  * step k: the trailing column norms over rows >= k are recomputed (fused
 //    into the previous step's update, no downdating); the pivot is the
-//    largest norm, the lowest position on exact ties;
+//    lowest position whose norm is at least the largest minus ID_TIE |R_00|
+//    (the largest times 1 - ID_TIE at step 0): columns that are mirror
+//    images on the grid have norms equal up to rounding, and the window makes
+//    the choice among them independent of how the norms were rounded;
 //  * the rank is the first k >= 1 with |R_kk| <= eps |R_00| (k = min(m, n)
 //    otherwise); an all-zero matrix gets rank 1 with V = e_0^T;
 //  * the reflector for column k is H = I - (2/v^H v) v v^H with
@@ -25,6 +28,7 @@ namespace hb {
 
 constexpr int ID_THREADS = 256;
 constexpr int ID_WARPS = ID_THREADS / 32;
+constexpr double ID_TIE = 1e-12;   // pivot tie window, relative to |R_00|
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -64,22 +68,35 @@ __global__ void __launch_bounds__(ID_THREADS) id_kernel(const int* __restrict__ 
   __syncthreads();
   const int kmax = min(m, n);
   for (int k = 0; k < kmax; ++k) {
-    if (threadIdx.x == 0) {
-      int p = k;
-      double best = nrm[k];
-      for (int j = k + 1; j < n; ++j)
-        if (nrm[j] > best) { best = nrm[j]; p = j; }
-      s_piv = p;
-      if (k == 0) {
-        s_r00 = best;
-        if (best == 0.0) { s_rank = 1; s_stop = 2; }
-      } else if (best <= eps * s_r00) {
-        s_rank = k;
-        s_stop = 1;
-      }
-      if (!s_stop && p != k) {
-        double t = nrm[k]; nrm[k] = nrm[p]; nrm[p] = t;
-        int q = perm[k]; perm[k] = perm[p]; perm[p] = q;
+    if (warp == 0) {
+      // the largest trailing norm, then the lowest position inside the tie
+      // window (both reductions are exact, so their order does not matter)
+      double top = 0.0;
+      for (int j = k + lane; j < n; j += 32) top = fmax(top, nrm[j]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) top = fmax(top, __shfl_xor_sync(0xffffffffu, top, o));
+      const double thr = (k == 0) ? top * (1.0 - ID_TIE) : top - ID_TIE * s_r00;
+      int p = n;
+      for (int j = k + lane; j < n; j += 32)
+        if (nrm[j] >= thr) {
+          p = j;
+          break;
+        }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) p = min(p, __shfl_xor_sync(0xffffffffu, p, o));
+      if (lane == 0) {
+        s_piv = p;
+        if (k == 0) {
+          s_r00 = nrm[p];
+          if (top == 0.0) { s_rank = 1; s_stop = 2; }
+        } else if (top <= eps * s_r00) {
+          s_rank = k;
+          s_stop = 1;
+        }
+        if (!s_stop && p != k) {
+          double t = nrm[k]; nrm[k] = nrm[p]; nrm[p] = t;
+          int q = perm[k]; perm[k] = perm[p]; perm[p] = q;
+        }
       }
     }
     __syncthreads();
@@ -229,6 +246,14 @@ void emit_v(int count, const int* d_m, const int* d_n, const long long* d_aoff, 
 // else is needed.  Every call overwrites the metadata it reads, so nothing
 // has to start at zero; calls that overlap on the GPU (different streams or
 // host threads without a synchronisation between them) race on the array.
+//
+// The caller's host arrays m, n, a_off are first copied into a file-scope
+// host array (ordinary pageable memory, under a mutex) and the device copies
+// read that array.  A copy from pageable memory has consumed its source when
+// cudaMemcpyAsync returns, so the caller may reuse its arrays on return even
+// when they are page-locked (a copy straight from page-locked memory would
+// read them only when the stream reaches it).
+#include <cstring>
 #include <mutex>
 
 namespace hb {
@@ -241,14 +266,16 @@ static __device__ __align__(256) unsigned char g_id_noalloc_scratch[ID_NOALLOC_B
 namespace {
 std::mutex g_noalloc_mu;
 void* g_noalloc_addr[256] = {};   // device address of the array, per device ordinal
+// host staging of the metadata (pageable; guarded by g_noalloc_mu)
+alignas(256) unsigned char g_noalloc_host[(size_t)ID_NOALLOC_MAX * 16];
 
 // Set-up, once per device, with that device current: look up the device
 // address of the array (its name in host code is only a host-side stand-in).
+// The caller holds g_noalloc_mu.
 void* noalloc_scratch() {
   int dev = 0;
   HB_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 256) throw Error{HB_ERR_UNSUPPORTED, "device ordinal above 255"};
-  std::lock_guard<std::mutex> lk(g_noalloc_mu);
   if (!g_noalloc_addr[dev]) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_id_noalloc_scratch);
@@ -309,15 +336,25 @@ void id_batch_noalloc(int count, const int* m, const int* n, const long long* a_
     max_n = std::max(max_n, n[b]);
   }
   if (count == 0) return;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
   unsigned char* base = static_cast<unsigned char*>(noalloc_scratch());
   int* d_m = reinterpret_cast<int*>(base);
   int* d_n = reinterpret_cast<int*>(base + (size_t)ID_NOALLOC_MAX * 4);
   long long* d_a = reinterpret_cast<long long*>(base + (size_t)ID_NOALLOC_MAX * 8);
   long long* d_s = reinterpret_cast<long long*>(base + (size_t)ID_NOALLOC_MAX * 16);
   long long* d_v = reinterpret_cast<long long*>(base + (size_t)ID_NOALLOC_MAX * 24);
-  HB_CUDA(cudaMemcpyAsync(d_m, m, sizeof(int) * count, cudaMemcpyHostToDevice, st));
-  HB_CUDA(cudaMemcpyAsync(d_n, n, sizeof(int) * count, cudaMemcpyHostToDevice, st));
-  HB_CUDA(cudaMemcpyAsync(d_a, a_off, sizeof(long long) * count, cudaMemcpyHostToDevice, st));
+  // one host-to-device copy of the staged metadata: m, n, a_off in the
+  // array's order (int m[MAX], int n[MAX], long long a_off[MAX]); only the
+  // first count entries of each part are copied
+  int* h_m = reinterpret_cast<int*>(g_noalloc_host);
+  int* h_n = reinterpret_cast<int*>(g_noalloc_host + (size_t)ID_NOALLOC_MAX * 4);
+  long long* h_a = reinterpret_cast<long long*>(g_noalloc_host + (size_t)ID_NOALLOC_MAX * 8);
+  std::memcpy(h_m, m, sizeof(int) * count);
+  std::memcpy(h_n, n, sizeof(int) * count);
+  std::memcpy(h_a, a_off, sizeof(long long) * count);
+  HB_CUDA(cudaMemcpyAsync(d_m, h_m, sizeof(int) * count, cudaMemcpyHostToDevice, st));
+  HB_CUDA(cudaMemcpyAsync(d_n, h_n, sizeof(int) * count, cudaMemcpyHostToDevice, st));
+  HB_CUDA(cudaMemcpyAsync(d_a, h_a, sizeof(long long) * count, cudaMemcpyHostToDevice, st));
   noalloc_offsets_kernel<<<1, 1024, 0, st>>>(d_n, count, d_s, d_v);
   HB_CHECK_LAUNCH();
   id_batch(count, d_m, d_n, d_a, A, eps, rank, skel, d_s, max_n, st);

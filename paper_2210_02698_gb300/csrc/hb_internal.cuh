@@ -168,6 +168,17 @@ struct BflyIndex {
   std::vector<long long> kl_off;
 };
 
+// A sampled block that hb_build decomposed, kept on request
+// (hb_record_id_blocks) so that a test can run the oracle's ID on exactly the
+// same samples.
+struct IdRecord {
+  int level = 0;                       // butterfly level k of the block
+  std::vector<long long> rows, cols;   // natural indices (proxy rows, column set)
+  std::vector<double2> A;              // rows x cols, column-major, as sampled
+  int rank = 0;
+  std::vector<int> piv;                // full pivot order (positions in cols)
+};
+
 // Host-side batch of ragged entry blocks (entries.cu).
 struct BlockMeta {
   long long row_off, m, col_off, n, out_off, seg_off, nseg, pad;
@@ -257,6 +268,10 @@ struct hb_ctx {
   double2* d_ks2v = nullptr;       // K^{s2v}, N_v x ns column-major
   double2* d_cy = nullptr;         // surface vectors of an apply, ns x cy_cap
   int cy_cap = 0;
+
+  // hb_record_id_blocks: blocks per butterfly level to keep, and the kept ones
+  int id_rec_per_level = 0;
+  std::vector<hb::IdRecord> id_recs;
 
   // timing
   bool timing = false;

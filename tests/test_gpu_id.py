@@ -67,3 +67,29 @@ def test_id_degenerate_cases():
         sk0, V0, _ = cpqr.cpqr_id(M, 1e-12)
         assert list(sk) == list(sk0)
         assert np.allclose(V, V0, atol=1e-12)
+
+
+def test_id_tie_window_matches_oracle():
+    """The constructed near-ties of the oracle's tie-window pin: the GPU
+    picks the same pivots (lowest position within TIE |R_00| of the largest
+    norm)."""
+    from oracle import cpqr
+    T = cpqr.TIE
+    rng = np.random.default_rng(17)
+    a = rng.standard_normal(6) + 1j * rng.standard_normal(6)
+    a /= np.linalg.norm(a)
+    e0 = np.zeros(5, dtype=complex)
+    e0[0] = 10.0
+    x = np.zeros(5, dtype=complex)
+    x[1:] = rng.standard_normal(4) + 1j * rng.standard_normal(4)
+    x /= np.linalg.norm(x)
+    y = np.zeros(5, dtype=complex)
+    y[1:] = np.roll(x[1:], 1) * np.exp(0.3j)
+    mats = [np.stack([a * (1 - 0.5 * T), a, 0.1 * a[::-1]], axis=1),
+            np.stack([a * (1 - 3 * T), a, 0.1 * a[::-1]], axis=1),
+            np.stack([e0, y * (1 - 0.5 * T * 10.0), x], axis=1),
+            np.stack([e0, y * (1 - 2.0 * T * 10.0), x], axis=1)]
+    got = _run(mats, 1e-14)
+    for M, (sk, V) in zip(mats, got):
+        sk0, _, _ = cpqr.cpqr_id(M, 1e-14)
+        assert list(sk) == list(sk0)

@@ -46,3 +46,38 @@ def test_ties_and_degenerate_cases():
     one = rng.standard_normal((1, 6)) + 0j
     sk, V, _ = cpqr.cpqr_id(one, 1e-6)
     assert len(sk) == 1 and np.allclose(one[:, sk] @ V, one)
+
+
+def test_tie_window_picks_the_lowest_position():
+    """Columns whose norms agree to within TIE |R_00| are tied and the lowest
+    position wins; a gap larger than the window is a real difference.  The
+    window is measured against |R_00|, not against the current largest norm
+    (step 1 below: a relative gap of 5e-12 against the column's own norm, but
+    half the window against |R_00| = 10)."""
+    T = cpqr.TIE
+    rng = np.random.default_rng(17)
+    a = rng.standard_normal(6) + 1j * rng.standard_normal(6)
+    a /= np.linalg.norm(a)
+    # step 0: the first column is smaller by half the window -> still chosen
+    M = np.stack([a * (1 - 0.5 * T), a, 0.1 * a[::-1]], axis=1)
+    assert cpqr.cpqr_id(M, 0.0)[0][0] == 0
+    # ... smaller by three windows -> the larger second column wins
+    M = np.stack([a * (1 - 3 * T), a, 0.1 * a[::-1]], axis=1)
+    assert cpqr.cpqr_id(M, 0.0)[0][0] == 1
+    # step 1: after the big first column, y (position 1) trails x (position 2)
+    # by 0.5 TIE |R_00| in absolute terms -> y; by 2 TIE |R_00| -> x
+    e0 = np.zeros(5, dtype=complex)
+    e0[0] = 10.0
+    x = np.zeros(5, dtype=complex)
+    x[1:] = rng.standard_normal(4) + 1j * rng.standard_normal(4)
+    x /= np.linalg.norm(x)
+    y = np.zeros(5, dtype=complex)
+    y[1:] = np.roll(x[1:], 1) * np.exp(0.3j)                 # same norm, other direction
+    for gap, want in ((0.5, 1), (2.0, 2)):
+        M = np.stack([e0, y * (1 - gap * T * 10.0), x], axis=1)
+        sk = cpqr.cpqr_id(M, 0.0)[0]
+        assert sk[0] == 0 and sk[1] == want, (gap, sk)
+    # the pivot helper itself
+    norms = np.array([1.0, 1.0 - 0.4 * T, 1.0 + 0.4 * T, 0.5])
+    assert cpqr.pivot(norms, 0, 0.0) == (0, 1.0 + 0.4 * T)
+    assert cpqr.pivot(norms[1:], 1, 1.0)[0] == 0
