@@ -258,8 +258,9 @@ def run_ours(args):
     build.build()
     w = W.WORKLOADS[args.workload]
     tab = load_tables(w)
+    tune = {"tuned": 1, "depth": 0, "dataflow": 2}[args.shape]
     op = binding.Operator(w.N, tab["nodes"], tab["tau2"], tab["v0"], tab["v1"], w.n_cells(), w.omega,
-                          eps=w.eps, leaf=w.leaf, chi=w.chi, precision=binding.HB_MIXED_BF16X3)
+                          eps=w.eps, leaf=w.leaf, chi=w.chi, precision=binding.HB_MIXED_BF16X3, autotune=tune)
     t0 = time.perf_counter()
     op.build()
     build_s = time.perf_counter() - t0
@@ -332,6 +333,26 @@ def run_ours(args):
     ktimes = op.kernel_times()
     op.set_kernel_timing(False)
 
+    # ---- measured FP64 peaks (the FP64 rooflines): the library's FMA-loop
+    # probe and a cuBLAS DGEMM (4096^3, best of three)
+    fp64_fma = binding.fp64_fma_peak(stream)
+    try:
+        A64 = torch.randn(4096, 4096, dtype=torch.float64, device=dev)
+        B64 = torch.randn(4096, 4096, dtype=torch.float64, device=dev)
+        torch.matmul(A64, B64)
+        best = 1e30
+        for _ in range(3):
+            g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            g0.record(stream)
+            torch.matmul(A64, B64)
+            g1.record(stream)
+            torch.cuda.synchronize()
+            best = min(best, g0.elapsed_time(g1))
+        fp64_dgemm = 2 * 4096 ** 3 / (best * 1e-3) / 1e12
+        del A64, B64
+    except Exception:
+        fp64_dgemm = None
+
     # ---- plain FP64 GPU butterfly apply (same factors, complex128)
     op.set_precision(binding.HB_FP64)
     apply64 = lambda: op.apply(s_dev, u_dev, R, stream)  # noqa: E731
@@ -348,8 +369,18 @@ def run_ours(args):
     if not large:
         apply_dense = lambda: op.apply_dense(s_dev, u_dev, R, stream)  # noqa: E731
         ms_dense = timed(apply_dense, 1, 1)
+        # counted FP64 flops per entry: tau^2, v0, v1 by 16-term contractions
+        # (48 FMA), the per-source-cell contraction shared by 64 outputs (12
+        # FMA per entry), the complex multiply-add per right-hand side (4 FMA);
+        # the Hankel evaluation is not counted, so the fraction is a lower bound
+        dflops = 2.0 * (48 + 12 + 4 * R) * float(Nv) * Nv
         dense_line = {"value": Nv * R * world / (ms_dense * 1e-3), "unit": UNIT, "ms_per_step": ms_dense,
-                      "rel_l2_mixed_vs_dense": float(torch.linalg.norm(u_mixed - u_dev) / torch.linalg.norm(u_dev))}
+                      "rel_l2_mixed_vs_dense": float(torch.linalg.norm(u_mixed - u_dev) / torch.linalg.norm(u_dev)),
+                      "roofline": {"bound": "alu", "achieved": dflops / (ms_dense * 1e-3) / 1e12,
+                                   "peak": fp64_fma, "unit": "TFLOP/s",
+                                   "frac": dflops / (ms_dense * 1e-3) / 1e12 / fp64_fma,
+                                   "flops_per_entry": 2 * (48 + 12 + 4 * R),
+                                   "peak_kind": "measured FP64 FMA loop (Hankel flops not counted)"}}
     op.set_precision(binding.HB_MIXED_BF16X3)
     u_mixed = None
 
@@ -432,11 +463,21 @@ def run_ours(args):
         gather_ms = sum(v[0] for k, v in ktimes.items() if k in ("gather", "scatter")) / nk
         E = info["factor_entries"]
         fac_bytes = E * 8
-        # algorithmic bytes of the step kernels of one apply: every factor entry
-        # once (8-byte split-BF16 pair), the tree-ordered input read once
-        # (8-byte pairs), the output written once (FP64 complex), every
-        # skeleton vector written once and read once (8-byte pairs)
-        alg_bytes = fac_bytes + Nv * R * (8 + 16) + 2 * info["skeleton_rows"] * R * 8
+        mt = min(2, (R + 15) // 16)
+        shape = op.launch_shape(False, mt)
+        passes = (R + 31) // 32
+        # algorithmic bytes of the timed kernels of one apply: every factor
+        # entry once (8-byte split-BF16 pair), the output written once (FP64
+        # complex), every skeleton vector written once and read once (8-byte
+        # pairs), and the input: read once as FP64 complex by the dataflow
+        # launch, which gathers it itself, or read once as the 8-byte pairs the
+        # separate gather wrote, when the step kernels run one launch per depth
+        in_bytes = 16 if shape["mode"] == 1 else 8
+        alg_bytes = fac_bytes + Nv * R * (in_bytes + 16) + 2 * info["skeleton_rows"] * R * 8
+        kernel_what = ("one persistent dataflow launch per pass of 32 right-hand sides (gather and every "
+                       "butterfly level)" if shape["mode"] == 1 else
+                       "butterfly step kernels of one apply (one launch per dependency depth)")
+        launches = passes * (1 if shape["mode"] == 1 else 1 + info["levels"] + 1)
         achieved = alg_bytes / (step_ms * 1e-3) / 1e9
         value = Nv * R * world / (ms * 1e-3)
         nc = cores()
@@ -500,7 +541,7 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": profiled_traffic(args.workload),
-                         "kernel": "butterfly step kernels of one apply (one launch per dependency depth)",
+                         "kernel": kernel_what,
                          "alg_bytes": alg_bytes, "kernel_ms": step_ms,
                          "peak_kind": f"{peak_kind} copy bandwidth"},
             "e2e": {"value": Nv * R * world / (ms_e2e * 1e-3), "unit": UNIT,
@@ -508,13 +549,21 @@ def run_ours(args):
                     "ms_per_step": ms_e2e,
                     "pipeline": f"copy-in, hb_apply, copy-out on three streams, {nbuf} device buffer pair(s)",
                     "result_equals_device_run": e2e_same},
-            "gpu_launches": info["apply_launches"] * args.steps,
+            "gpu_launches": launches * args.steps,
+            "launch_shape": {**shape, "requested": args.shape},
             "timed": "CUDA-graph replay of hb_apply" if ms_graph is not None else graph_note,
             "eager_ms_per_step": ms_eager,
             "clocks": clk,
             "cpu_baseline": cpu,
             "cpu_butterfly": cpu_bf,
-            "fp64_gpu": {"value": Nv * R * world / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64},
+            "fp64_gpu": {"value": Nv * R * world / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64,
+                         "roofline": {"bound": "alu", "achieved": 8.0 * E * R / (ms64 * 1e-3) / 1e12,
+                                      "peak": fp64_fma, "unit": "TFLOP/s",
+                                      "frac": 8.0 * E * R / (ms64 * 1e-3) / 1e12 / fp64_fma,
+                                      "flops": "8 per stored complex factor entry and right-hand side",
+                                      "peak_kind": "measured FP64 FMA loop"}},
+            "fp64_peaks": {"fma_loop_tflops": fp64_fma, "dgemm_tflops": fp64_dgemm,
+                           "note": "measured in this run: the library's FMA-loop probe; cuBLAS DGEMM 4096^3"},
             "fp64_gpu_dense": dense_line,
             "speedup_vs_fp64_gpu": ms64 / ms,
             "rel_l2_mixed_vs_fp64_butterfly": rel_mixed_fp64,
@@ -543,6 +592,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(W.WORKLOADS))
     ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU oracle leg (profiling runs)")
+    ap.add_argument("--shape", default="tuned", choices=["tuned", "dataflow", "depth"],
+                    help="launch shape of the mixed apply: autotuned (default), the persistent dataflow "
+                         "launch, or one launch per dependency depth")
     ap.add_argument("--one-core-sample", nargs=3, metavar=("WORKLOAD", "ROWS", "SEED"), help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.one_core_sample:

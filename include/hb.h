@@ -87,7 +87,19 @@ typedef struct {
  * kernel then lets its copies in flight land (waiting at least 2^31 cycles
  * for them) and stops; a later hb_apply / hb_apply_adjoint on the handle,
  * called once the device has run the apply that ran out, returns
- * HB_ERR_TIMEOUT (the outputs of the apply that ran out are undefined). */
+ * HB_ERR_TIMEOUT (the outputs of the apply that ran out are undefined).
+ * autotune: 0 = the default launch shape of the mixed apply (a gather and
+ * one launch per dependency depth, 16 KB items); 1 = the first
+ * mixed apply of each direction and m-tile count (16 right-hand sides per
+ * m-tile) times every candidate shape on the caller's stream (one launch per
+ * dependency depth at 16 KB or 8 KB items; one persistent launch at 16 KB or
+ * 8 KB items, placement slack 16, 48 or 128 cost units, 1 or 4 chains per
+ * flag publication; each a full apply, best of three) and keeps the fastest
+ * (hb_launch_shape reports it).  That first apply then blocks the host for
+ * the tuning (milliseconds to seconds, growing with N_v); under stream
+ * capture no tuning happens and the default shape is used.  2 = always the
+ * persistent dataflow launch (16 KB items, slack 48, one chain per
+ * publication). */
 typedef struct {
   double eps;
   int leaf;
@@ -96,6 +108,7 @@ typedef struct {
   int precision;
   int workspace_mb;
   long long barrier_cycles;
+  int autotune;
 } hb_options;
 
 /* Statistics filled by hb_info. */
@@ -112,7 +125,11 @@ typedef struct {
   double build_ms;
   int built;
   int apply_launches;         /* kernels launched by one mixed-precision
-                                 hb_apply of up to 32 right-hand sides     */
+                                 hb_apply of up to 32 right-hand sides in
+                                 the default launch shape (the gather and
+                                 one launch per dependency depth;
+                                 hb_launch_shape says which shape an apply
+                                 actually used)                            */
   long long skeleton_rows;    /* sum of all ranks: rows of skeleton vectors */
 } hb_stats;
 
@@ -295,6 +312,29 @@ hb_status hb_id_batch(int count, const int* m, const int* n, const long long* a_
  * synchronisation in between) race on it. */
 hb_status hb_id_batch_noalloc(int count, const int* m, const int* n, const long long* a_off,
                               void* A, double eps, int* rank, int* skel, void* V, void* stream);
+
+/* hb_fp64_fma_peak: the measured FP64 rate of the current device in
+ * TFLOP/s (2 flops per fused multiply-add), from a kernel of independent
+ * FMA recurrences filling every SM, timed with CUDA events on `stream`
+ * (best of three after a warm-up run; synchronous, ~milliseconds).  The
+ * denominator of the FP64 rooflines (the paper's method has no counterpart:
+ * a measurement utility).  Errors: HB_ERR_ARG, HB_ERR_CUDA. */
+hb_status hb_fp64_fma_peak(double* tflops, void* stream);
+
+/* hb_launch_shape: the launch shape the mixed apply uses for one direction
+ * (adjoint 0 or 1) and m-tile count (mtiles 1: up to 16 right-hand sides
+ * per pass, 2: up to 32): *mode = 0 for a gather plus one launch per
+ * dependency depth, 1 for one persistent dataflow launch (the gather
+ * inside), -1 if no apply has run yet at that m-tile count; *item_bytes the
+ * item size the accumulation chains are cut to, *stages the shared-memory
+ * ring stages per warp, *pub_batch the chains a dataflow warp publishes
+ * together, *slack the dataflow placement's margin between a producer's
+ * simulated finish and its consumers (cost units: one per 512-byte factor
+ * tile, four per item), *tuned_ms the autotuner's time for the chosen shape
+ * (0 when it did not run) and *candidates the shapes it timed.
+ * HB_ERR_STATE before hb_build. */
+hb_status hb_launch_shape(hb_handle h, int adjoint, int mtiles, int* mode, int* item_bytes, int* stages,
+                          int* pub_batch, int* slack, double* tuned_ms, int* candidates);
 
 /* hb_record_id_blocks / hb_recorded_id_count / hb_recorded_id_block: keep,
  * for a check of the interpolative decomposition (Sec. 4.2.1, Eq. ID, on the

@@ -25,7 +25,7 @@ EXPORTS = ["hb_create", "hb_build", "hb_save", "hb_load", "hb_apply", "hb_apply_
            "hb_set_wait_selftest", "hb_device_alloc_cap",
            "hb_apply_dense", "hb_apply_dense_adjoint", "hb_entries", "hb_curve_set", "hb_curve_operators",
            "hb_apply_inclusion", "hb_id_batch", "hb_id_batch_noalloc",
-           "hb_record_id_blocks", "hb_recorded_id_count", "hb_recorded_id_block",
+           "hb_record_id_blocks", "hb_recorded_id_count", "hb_recorded_id_block", "hb_launch_shape", "hb_fp64_fma_peak",
            "hb_tree_perm", "hb_proxy_rows", "hb_host_cluster_tree", "hb_host_proxy_rows", "hb_host_segment_tree", "hb_host_point_proxy_rows", "hb_info", "hb_rank_profile", "hb_set_kernel_timing",
            "hb_kernel_times", "hb_last_error", "hb_destroy"]
 
@@ -44,7 +44,7 @@ class Tables(C.Structure):
 class Options(C.Structure):
     _fields_ = [("eps", C.c_double), ("leaf", C.c_int), ("chi", C.c_double),
                 ("nbr_radius_h", C.c_double), ("precision", C.c_int), ("workspace_mb", C.c_int),
-                ("barrier_cycles", C.c_longlong)]
+                ("barrier_cycles", C.c_longlong), ("autotune", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -81,6 +81,9 @@ def lib():
         L.hb_apply_inclusion.argtypes = [vp, vp, vp, i, i, vp]
         L.hb_id_batch.argtypes = [i, vp, vp, vp, vp, d, vp, vp, vp]
         L.hb_id_batch_noalloc.argtypes = [i, vp, vp, vp, vp, d, vp, vp, vp, vp]
+        L.hb_launch_shape.argtypes = [vp, i, i, C.POINTER(i), C.POINTER(i), C.POINTER(i), C.POINTER(i),
+                                      C.POINTER(i), C.POINTER(d), C.POINTER(i)]
+        L.hb_fp64_fma_peak.argtypes = [C.POINTER(d), vp]
         L.hb_record_id_blocks.argtypes = [vp, i]
         L.hb_recorded_id_count.argtypes = [vp, C.POINTER(i)]
         L.hb_recorded_id_block.argtypes = [vp, i, C.POINTER(i), C.POINTER(i), C.POINTER(i), vp, vp, vp,
@@ -153,7 +156,7 @@ class Operator:
 
     def __init__(self, N, nodes, tau2, v0, v1, n_cells, omega, eps=1e-6, leaf=64, chi=20.0,
                  nbr_radius_h=10.0, precision=HB_MIXED_BF16X3, workspace_mb=0, h=None,
-                 x0=0.0, y0=0.0, barrier_cycles=0):
+                 x0=0.0, y0=0.0, barrier_cycles=0, autotune=0):
         L = lib()
         self._keep = [np.ascontiguousarray(a, dtype=np.float64) for a in (nodes, tau2, v0, v1, n_cells)]
         nodes, tau2, v0, v1, n_cells = self._keep
@@ -164,7 +167,7 @@ class Operator:
         g = Grid(nx, ny, x0, y0, self.h)
         t = Tables(len(nodes), nodes.ctypes.data, nodes.ctypes.data, tau2.ctypes.data,
                    v0.ctypes.data, v1.ctypes.data, n_cells.ctypes.data)
-        o = Options(eps, leaf, chi, nbr_radius_h, precision, workspace_mb, int(barrier_cycles))
+        o = Options(eps, leaf, chi, nbr_radius_h, precision, workspace_mb, int(barrier_cycles), int(autotune))
         hnd = C.c_void_p()
         _check(L.hb_create(C.byref(g), C.byref(t), float(omega), C.byref(o), C.byref(hnd)))
         self.handle = hnd
@@ -270,6 +273,16 @@ class Operator:
         self._call("hb_proxy_rows", int(t0), int(t1), seeds.ctypes.data, len(seeds), out.ctypes.data,
                    C.byref(cnt))
         return out[:cnt.value].copy()
+
+    def launch_shape(self, adjoint=False, mtiles=1):
+        """hb_launch_shape: the mixed apply's launch shape for one direction
+        and m-tile count (mode -1 before the first apply at that count)."""
+        mode, ib, st, pub, sl, cand = C.c_int(), C.c_int(), C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        ms = C.c_double()
+        self._call("hb_launch_shape", 1 if adjoint else 0, int(mtiles), C.byref(mode), C.byref(ib), C.byref(st),
+                   C.byref(pub), C.byref(sl), C.byref(ms), C.byref(cand))
+        return {"mode": mode.value, "item_bytes": ib.value, "stages": st.value, "pub_batch": pub.value,
+                "slack": sl.value, "tuned_ms": ms.value, "candidates": cand.value}
 
     def record_id_blocks(self, per_level):
         """hb_record_id_blocks: before build(), keep up to per_level of the
@@ -407,6 +420,13 @@ def id_batch_noalloc(A, m, n, a_off, eps, rank, skel, V, stream=None):
     m, n, a_off, (pA, pr, ps, pV) = _id_args(A, m, n, a_off, rank, skel, V)
     _check(lib().hb_id_batch_noalloc(len(m), m.ctypes.data, n.ctypes.data, a_off.ctypes.data, pA,
                                      float(eps), pr, ps, pV, _stream_ptr(stream)))
+
+
+def fp64_fma_peak(stream=None):
+    """hb_fp64_fma_peak: measured FP64 TFLOP/s of the current device."""
+    v = C.c_double()
+    _check(lib().hb_fp64_fma_peak(C.byref(v), _stream_ptr(stream)))
+    return v.value
 
 
 def load_tables(path):

@@ -112,7 +112,7 @@ void free_all(hb_ctx* c) {
   for (void* p : {(void*)c->d_nodes, (void*)c->d_tab, (void*)c->d_LX, (void*)c->d_LZ, (void*)c->d_H[0],
                   (void*)c->d_H[1], (void*)c->d_ncell, (void*)c->d_self, (void*)c->d_perm, (void*)c->d_f64,
                   (void*)c->d_nat[0], (void*)c->d_nat[1], (void*)c->d_pperm, (void*)c->d_mx,
-                  (void*)c->d_mxh, c->d_x, c->d_y, (void*)c->d_dense_part})
+                  (void*)c->d_mxh, c->d_x, c->d_y, (void*)c->d_dense_part, (void*)c->d_flags})
     hb::dev_free(p);
   hb::dev_free(c->d_xh);
   hb::dev_free(c->d_tasks[0]);
@@ -152,6 +152,7 @@ hb_ctx* create_ctx(const hb_grid* grid, const hb_tables* tables, double omega, c
     throw hb::arg_error("bad options (eps > 0, leaf >= 1, chi > 0, radius >= 0)");
   if (opts->precision != HB_FP64 && opts->precision != HB_MIXED_BF16X3)
     throw hb::arg_error("unknown precision %d", opts->precision);
+  if (opts->autotune < 0 || opts->autotune > 2) throw hb::arg_error("autotune must be 0, 1 or 2");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
     cudaGetLastError();
@@ -284,6 +285,18 @@ hb_status hb_recorded_id_block(hb_handle h, int index, int* level, int* m, int* 
     if (cols) std::copy(r.cols.begin(), r.cols.end(), cols);
     if (A) std::copy(r.A.begin(), r.A.end(), static_cast<double2*>(A));
     if (pivots) std::copy(r.piv.begin(), r.piv.end(), pivots);
+  });
+}
+
+hb_status hb_launch_shape(hb_handle h, int adjoint, int mtiles, int* mode, int* item_bytes, int* stages,
+                          int* pub_batch, int* slack, double* tuned_ms, int* candidates) {
+  return guarded(h, [&] {
+    if (!h || !mode || !item_bytes || !stages || !pub_batch || !slack || !tuned_ms || !candidates)
+      throw hb::arg_error("null argument");
+    if (adjoint != 0 && adjoint != 1) throw hb::arg_error("adjoint must be 0 or 1");
+    if (mtiles != 1 && mtiles != 2) throw hb::arg_error("mtiles must be 1 or 2");
+    if (!h->built || !h->flow_plan[adjoint]) throw hb::Error{HB_ERR_STATE, "not built"};
+    hb::flow_shape(h->flow_plan[adjoint], mtiles, mode, item_bytes, stages, pub_batch, slack, tuned_ms, candidates);
   });
 }
 

@@ -57,6 +57,7 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
+#include <map>
 #include <numeric>
 #include <queue>
 #include <vector>
@@ -453,6 +454,327 @@ __global__ void __launch_bounds__(NWARP * 32, 1) bf_step_kernel(StepArgs a) {
   if (lane == 0) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// ------------------------------------------------ persistent dataflow ----
+// One launch per apply: every warp runs its stream of chains of ALL depths,
+// and a chain waits only for the row tiles it reads, not for a whole depth.
+// Readiness is a per-row-tile flag (x tiles then xh tiles) holding the
+// number of the launch that last wrote the tile; a launch writes
+// target = (launches completed) + 1, so no flag is ever reset.
+//
+// Producers: the lanes of a warp store a chain's output tiles, fence, and
+// set the tiles' flags (after pub_batch chains, or earlier when the warp is
+// about to wait).  Consumers: the flags of an item's input tiles are read
+// once when its record window is loaded (32 items ahead); an item found
+// ready there, or at its refill, gets both copies at once; otherwise its
+// factor run goes out and its input run is issued when the item is next to
+// compute, after a bounded wait on the flags.
+//
+// Deadlock freedom.  The host places the chains by simulating the schedule
+// (chains in order of their simulated ready time, each on the stream that
+// frees first), so every stream runs its chains in increasing simulated
+// start time and every producer starts before its consumers.  A warp waits
+// on flags only for the item it must compute next, with all its earlier
+// chains stored and published; the gather slices are published before any
+// warp waits.  A waiting warp's producer therefore starts strictly earlier
+// in the simulated order than the waiting chain, and the warp holding that
+// producer is either running or waiting on a strictly earlier chain: no
+// cycle.  The launch is cooperative, so all CTAs are resident together.
+struct FlowArgs {
+  StepArgs a;
+  const double2* s;     // FP64 input in natural order (gathered here)
+  double scale;
+  long long nv_tiles;   // flags [0, nv_tiles): x row tiles; nv_tiles + t: xh row tile t
+  unsigned* flags;
+  unsigned* epoch;      // [0] launches completed, [1] CTAs finished in this launch
+  int pub_batch;        // chains whose flags are set together
+};
+
+constexpr int PUB_MAX = 64;   // pending output tiles per warp
+
+__device__ __forceinline__ unsigned ld_flag(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_flag(unsigned* p, unsigned v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// x (native) tile (rt, mt) = pairs of scale * s at the padded rows of row
+// tile rt, one warp (as gather_native_kernel, through the warp's scratch)
+template <int MT>
+__device__ __forceinline__ void gather_tile(const FlowArgs& f, long long rt, int lane, uint32_t* tile) {
+  const int r = lane & 7, c0 = 4 * (lane >> 3);
+  const long long nat = f.a.pperm[8 * rt + r];
+#pragma unroll
+  for (int mt = 0; mt < MT; ++mt) {
+    double2 v[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int rhs = 16 * mt + c0 + c;
+      v[c] = (nat >= 0 && rhs < f.a.R) ? f.s[(size_t)rhs * f.a.Nv + nat] : make_double2(0.0, 0.0);
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int q = c0 + c;
+      const int dl = (q & 7) * 4 + (r >> 1);
+      const int dj = (r & 1) * 2 + (q >> 3);
+      const uint2 p = to_pair((float)(v[c].x * f.scale), (float)(v[c].y * f.scale));
+      tile[dl * 4 + dj] = p.x;
+      tile[128 + dl * 4 + dj] = p.y;
+    }
+    __syncwarp();
+    uint4* out = f.a.x + ((size_t)rt * MT + mt) * 64;
+    out[lane] = reinterpret_cast<const uint4*>(tile)[lane];
+    out[32 + lane] = reinterpret_cast<const uint4*>(tile)[32 + lane];
+    __syncwarp();
+  }
+}
+
+template <int MT>
+__global__ void __launch_bounds__(NWARP * 32, 1) bf_flow_kernel(FlowArgs f) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ uint64_t full[NWARP][MAX_STAGES];
+  __shared__ __align__(16) WItem slot[NWARP][MAX_STAGES];
+  __shared__ __align__(16) int4 recs[NWARP][32][2];
+  __shared__ __align__(16) uint32_t gtile[NWARP][256];
+  __shared__ int pubs[NWARP][PUB_MAX];
+  __shared__ unsigned s_target;
+  __shared__ uint64_t never;   // failure-detection self-test: nothing arrives on it
+  const StepArgs& a = f.a;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nst = a.stages;
+  auto buf = [&](int id) { return id == 0 ? a.x : a.xh; };
+  const long long sid = (long long)blockIdx.x * NWARP + warp;
+  const long long nstreams = (long long)gridDim.x * NWARP;
+  const long long ib = a.off[sid], n = a.off[sid + 1] - ib;
+  unsigned char* ring = smem + (size_t)warp * nst * a.stage_bytes;
+  uint64_t* bar = full[warp];
+  WItem* sl = slot[warp];
+  if (threadIdx.x == 0) s_target = *reinterpret_cast<volatile unsigned*>(f.epoch) + 1u;
+  if (lane == 0) {
+    for (int s = 0; s < nst; ++s) mbar_init(&bar[s], 1);
+    if (warp == 0) mbar_init(&never, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const unsigned target = s_target;
+  const long long deadline = clock64() + a.budget;
+  const uint64_t pol_f = policy_evict_first(), pol_v = policy_evict_last();
+
+  // flags of an item's input tiles: all lanes, warp-uniform result
+  auto inputs_ready = [&](const WItem& w) {
+    bool ok = true;
+    const unsigned* fl = f.flags + (w.x_buf == 0 ? 0 : f.nv_tiles) + w.x_tile;
+    for (int j = lane; j < w.ks; j += 32) ok = ok && ld_flag(fl + j) == target;
+    return __all_sync(0xffffffffu, ok);
+  };
+
+  int4 w0lo = make_int4(0, 0, 0, 0), w0hi = w0lo, w1lo = w0lo, w1hi = w0lo;
+  auto load_win = [&](long long w) {
+    const long long q = 32 * w + lane;
+    if (q < n) {
+      const int4* r = reinterpret_cast<const int4*>(a.items + ib + q);
+      if (w & 1) {
+        w1lo = r[0];
+        w1hi = r[1];
+      } else {
+        w0lo = r[0];
+        w0hi = r[1];
+      }
+    }
+  };
+  load_win(0);
+  load_win(1);
+  auto f_bytes = [](const WItem& w) { return (uint32_t)w.ntl * (uint32_t)w.ks * 512u; };
+  auto x_bytes = [](const WItem& w) { return (uint32_t)w.ks * (uint32_t)(MT * 1024); };
+  // move the window of item q to shared memory; each lane checks the flags
+  // of its record's inputs there and marks the record ready (pad = 1)
+  auto move_window = [&](long long q) {
+    const bool odd = (q >> 5) & 1;
+    int4 lo = odd ? w1lo : w0lo, hi = odd ? w1hi : w0hi;
+    const int ks = hi.z & 0xffff, xb = hi.w & 0xff;
+    const long long xt = (long long)(((unsigned long long)(unsigned)lo.w << 32) | (unsigned)lo.z);
+    const unsigned* fl = f.flags + (xb == 0 ? 0 : f.nv_tiles) + xt;
+    bool ok = true;
+    for (int j0 = 0; j0 < ks; j0 += 8) {   // loads issued together, compared after
+      unsigned v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = (j0 + j < ks) ? ld_flag(fl + j0 + j) : target;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) ok = ok && v[j] == target;
+    }
+    hi.w = (hi.w & 0xffff) | (ok ? 0x10000 : 0);
+    recs[warp][lane][0] = lo;
+    recs[warp][lane][1] = hi;
+    __syncwarp();
+    if (q >= 32) load_win((q >> 5) + 1);
+  };
+  // stage s gets item q: lane 0 stores the record, arms the barrier for both
+  // runs and fetches the factor run, and the input run when the record was
+  // found ready (may_x); returns false (warp-uniform) when the input run is
+  // left pending
+  auto issue = [&](int s, long long q, bool may_x) {
+    if ((q & 31) == 0) move_window(q);
+    const int4 lo = recs[warp][q & 31][0], hi = recs[warp][q & 31][1];
+    WItem w;
+    reinterpret_cast<int4*>(&w)[0] = lo;
+    reinterpret_cast<int4*>(&w)[1] = hi;
+    const bool xok = w.ks == 0 || (may_x && w.pad != 0);
+    if (lane == 0) {
+      sl[s] = w;
+      unsigned char* st = ring + (size_t)s * a.stage_bytes;
+      mbar_expect_tx(&bar[s], f_bytes(w) + x_bytes(w));
+      if (w.ks) {
+        tma_load_1d(st, a.F + w.f_tile * 32, f_bytes(w), &bar[s], pol_f);
+        if (xok) {
+          asm volatile("fence.proxy.async.global;" ::: "memory");
+          tma_load_1d(st + f_bytes(w), buf(w.x_buf) + w.x_tile * (MT * 64), x_bytes(w), &bar[s], pol_v);
+        }
+      }
+    }
+    return xok;
+  };
+  auto issue_x = [&](int s) {   // lane 0: the pending input run of stage s
+    const WItem& w = sl[s];
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    tma_load_1d(ring + (size_t)s * a.stage_bytes + f_bytes(w), buf(w.x_buf) + w.x_tile * (MT * 64), x_bytes(w),
+                &bar[s], pol_v);
+  };
+
+  // output tiles stored but not yet flagged
+  int npub = 0, nchains = 0;
+  auto publish = [&]() {
+    if (npub == 0) return;
+    __threadfence();
+    __syncwarp();
+    for (int j = lane; j < npub; j += 32) st_flag(f.flags + f.nv_tiles + pubs[warp][j], target);
+    __syncwarp();
+    npub = 0;
+    nchains = 0;
+  };
+
+  // prologue: factor runs of the first items, then this warp's slice of the
+  // gather (published at once), then the first input runs
+  const long long pro = n < nst ? n : nst;
+  unsigned pend = 0;
+  for (long long q = 0; q < pro; ++q) issue((int)q, q, false);
+  {
+    const long long g0 = f.nv_tiles * sid / nstreams, g1 = f.nv_tiles * (sid + 1) / nstreams;
+    for (long long rt = g0; rt < g1; ++rt) gather_tile<MT>(f, rt, lane, gtile[warp]);
+    __threadfence();
+    __syncwarp();
+    for (long long rt = g0 + lane; rt < g1; rt += 32) st_flag(f.flags + rt, target);
+    __syncwarp();
+  }
+  for (long long q = 0; q < pro; ++q)
+    if (sl[q].ks) pend |= 1u << q;   // polled below like any pending stage
+  __syncwarp();
+
+  float acc[NTW][MT][8];
+  zero_acc<MT>(acc);
+  long long i = 0;
+  bool timed_out = false;
+  // Pending stages are polled without stalling: lane j reads the flag of
+  // input tile j % 8 of stage j / 8 before the item's products and the
+  // values are looked at after them (stages with more than 8 input tiles
+  // wait until they are next).
+  const int pst = lane >> 3, ptl = lane & 7;
+  for (; i < n; ++i) {
+    const int s = (int)(i % nst);
+    unsigned pv = target;
+    if (((pend >> pst) & 1u) && pst != s && pst < nst) {
+      const WItem& w = sl[pst];
+      if (w.ks <= 8 && ptl < w.ks) pv = ld_flag(f.flags + (w.x_buf == 0 ? 0 : f.nv_tiles) + w.x_tile + ptl);
+    }
+    if ((pend >> s) & 1u) {
+      // next to compute: publish, then wait (bounded) for the input tiles
+      publish();
+      bool ok = false;
+      while (!(ok = inputs_ready(sl[s])))
+        if (clock64() > deadline) break;
+      if (lane == 0) issue_x(s);   // also after a timeout: in bounds, so the stage completes
+      pend &= ~(1u << s);
+      if (!ok) {
+        timed_out = true;
+        break;
+      }
+    }
+    const bool ok = mbar_wait_until(&bar[s], (uint32_t)((i / nst) & 1), deadline);
+    if (!__all_sync(0xffffffffu, ok)) {
+      timed_out = true;
+      break;
+    }
+    const WItem& w = sl[s];
+    const int flags = w.flags, ntl = w.ntl, ks = w.ks;
+    const uint4* st = reinterpret_cast<const uint4*>(ring + (size_t)s * a.stage_bytes);
+    if (flags & 1) zero_acc<MT>(acc);
+    if (ks > 0) item_mma<MT>(st, st + ntl * ks * 32, ks, ntl, lane, acc);
+    // pending stages whose tiles all showed ready get their input runs
+    const unsigned bad = __ballot_sync(0xffffffffu, pv != target);
+    unsigned go = 0;
+    for (int t = 0; t < nst; ++t)
+      if (((pend >> t) & 1u) && t != s && sl[t].ks <= 8 && ((bad >> (8 * t)) & 0xffu) == 0) go |= 1u << t;
+    if (go) {
+      if (lane == 0)
+        for (int t = 0; t < nst; ++t)
+          if ((go >> t) & 1u) issue_x(t);
+      pend &= ~go;
+    }
+    // chains stored by earlier items: their stores have had this item's
+    // products to land, so the fence before their flags is short
+    if (nchains >= f.pub_batch) publish();
+    if (flags & 2) {
+      if (w.y_buf == 1) {
+        store_natural<MT>(a, w.y_tile, ntl, lane, acc);
+      } else {
+        store_tiles<MT>(a.xh + (size_t)w.y_tile * (MT * 64), ntl, lane, acc, pol_v);
+        if (npub + ntl > PUB_MAX) publish();
+        if (lane < ntl) pubs[warp][npub + lane] = (int)(w.y_tile + lane);
+        npub += ntl;
+        ++nchains;
+      }
+    }
+    __syncwarp();
+    if (i + nst < n && !issue(s, i + nst, true)) pend |= 1u << s;
+    __syncwarp();
+  }
+  publish();
+  if (timed_out) {
+    // report, issue every pending input run (in bounds) so that every stage
+    // completes, let the copies in flight land, stop
+    if (lane == 0) {
+      *reinterpret_cast<volatile int*>(a.err) = 1;
+      for (int t = 0; t < nst; ++t)
+        if ((pend >> t) & 1u) issue_x(t);
+      const long long last = (i + nst < n) ? i + nst : n;
+      const long long drain = a.budget > (1LL << 31) ? a.budget : (1LL << 31);
+      for (long long j = i; j < last; ++j)
+        mbar_wait_until(&bar[j % nst], (uint32_t)((j / nst) & 1), clock64() + drain);
+    }
+    __syncwarp();
+  }
+  // failure-detection self-test: after its stream (so that no chain that
+  // other warps wait for is held back), the first warp waits, through the
+  // same bounded wait, on a barrier nothing completes
+  if (a.selftest && blockIdx.x == 0 && warp == 0) {
+    const bool ok = mbar_wait_until(&never, 0u, clock64() + a.budget);
+    if (lane == 0 && !ok) *reinterpret_cast<volatile int*>(a.err) = 1;
+    __syncwarp();
+  }
+  // the last CTA to finish counts the launch as completed
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned done = atomicAdd(f.epoch + 1, 1u);
+    if (done == gridDim.x - 1) {
+      f.epoch[1] = 0;
+      __threadfence();
+      *reinterpret_cast<volatile unsigned*>(f.epoch) = target;
+    }
+  }
+}
+
 // --------------------------------------------------- conversions / I/O ----
 __device__ __forceinline__ int part_index(int pos, int r1, int r2) {
   const int p1 = (r1 + 7) & ~7;
@@ -577,66 +899,50 @@ struct DepthStreams {
   long long* d_off = nullptr;
 };
 
-struct LaunchShape {   // per m-tile count, set on first use
+// The launch shape of one m-tile count: the mode (one launch per depth, or
+// one persistent dataflow launch), the item size the chains are cut to, the
+// ring stages that fit, the grid, and how many chains a dataflow warp
+// publishes together.  Chosen by the autotuner on the first apply (when
+// hb_options.autotune is set) or set to the defaults.
+struct LaunchShape {
   bool ready = false;
+  int mode = 0;
+  int item_bytes = ITEM_BYTES;
   int stage = 0, stages = 0, grid = 0;
+  int pub = 2;
+  int slack = 48;        // dataflow placement: cost units between a producer's finish and its consumer
   size_t smem = 0;
+  double tuned_ms = 0;   // the chosen candidate's time (0: not tuned)
+  int candidates = 0;    // candidates the autotuner timed
 };
 
-// Everything below is kept per m-tile count MT (index 1 or 2): the items are
-// cut so that NWARP warps x 2 stages of the largest item fit in shared memory.
+// Chains cut for one (m-tile count, item size) with their warp streams.
+struct ChainSet {
+  int stage_bytes = 512;                                   // largest item (factor run + input run)
+  std::vector<std::vector<std::vector<WItem>>> by_depth;   // [depth][chain] -> items
+  int depth_grid = 0;
+  std::vector<DepthStreams> depth_streams;                 // mode 0: one stream set per depth
+  int flow_grid = 0;
+  std::map<int, DepthStreams> flow_streams;                // mode 1: all depths in one stream set, per slack
+};
+
+// The terms of every task, uncut, kept per depth as "term chains": one
+// WItem per term (ks = all of its k-steps) for each n-tile group; cut into
+// items per (m-tile count, item size) on demand.
 struct FlowPlan {
-  // chains of every depth: the items of one chain, in order
-  std::vector<std::vector<std::vector<WItem>>> chains[3];
-  int stage_bytes[3] = {0, 512, 512};     // largest item (factor run + input run)
-  int grid[3] = {0, 0, 0};                // CTAs the streams were dealt for
+  std::vector<std::vector<std::vector<WItem>>> terms;   // [depth][group chain] -> uncut terms
+  long long xh_tiles = 0;                               // row tiles the plan writes in xh
+  std::map<std::pair<int, int>, ChainSet> sets;         // (MT, item bytes) -> chains
   LaunchShape shape[3];
-  std::vector<DepthStreams> streams[3];
 };
 
-// k-steps per item for groups of ntl n-tiles: at one m-tile, ITEM_BYTES
-// bounds the factor run plus the input run counted at two m-tiles (so an
-// item is at most 12 KB); at two m-tiles the bound is 13 KB (an item is then
-// at most 12.5 KB, and 8 warps x 2 stages fit in 227 KB beside the record
-// windows).
-static int item_ks(int ntl, int MT) {
-  return std::max(1, (MT == 1 ? ITEM_BYTES : 13312) / (512 * ntl + 2048));
-}
-
-// The chains of one task for MT m-tiles: group g holds n-tiles
-// [g ng, g ng + ntl); each term contributes its k-steps in runs of at most
-// item_ks(ntl, MT).
-static void task_chains(const NatTask& L, int MT, std::vector<std::vector<WItem>>& out, int& stage_bytes) {
-  if (L.ng < 1 || L.ng > NTW) throw Error{HB_ERR_UNSUPPORTED, "n-tile group larger than the accumulators"};
-  const int ngr = (L.nt + L.ng - 1) / L.ng;
-  for (int g = 0; g < ngr; ++g) {
-    const int ntl = std::min(L.ng, L.nt - g * L.ng);
-    const int kc = item_ks(ntl, MT);
-    std::vector<WItem> ch;
-    for (const NatTerm& tm : L.terms)
-      for (int k0 = 0; k0 < tm.ks; k0 += kc) {
-        WItem w{};
-        w.f_tile = tm.f_tile + (long long)g * L.ng * tm.ks + (long long)k0 * ntl;
-        w.x_tile = tm.x_tile + k0;
-        w.y_tile = L.y_tile + (long long)g * L.ng;
-        w.ks = (short)std::min(kc, tm.ks - k0);
-        w.ntl = (unsigned char)ntl;
-        w.x_buf = (unsigned char)tm.x_buf;
-        w.y_buf = (unsigned char)L.y_buf;
-        ch.push_back(w);
-        stage_bytes = std::max(stage_bytes, ntl * (int)w.ks * 512 + (int)w.ks * MT * 1024);
-      }
-    if (ch.empty()) {   // every input is empty: the group is zero
-      WItem w{};
-      w.y_tile = L.y_tile + (long long)g * L.ng;
-      w.ntl = (unsigned char)ntl;
-      w.y_buf = (unsigned char)L.y_buf;
-      ch.push_back(w);
-    }
-    ch.front().flags |= 1;
-    ch.back().flags |= 2;
-    out.push_back(std::move(ch));
-  }
+// k-steps per item for groups of ntl n-tiles: the factor run plus the input
+// run counted at two m-tiles stays within item_bytes at one m-tile and
+// within 13/16 of it at two (so that the largest items at two m-tiles, the
+// 12.5 KB of the default 16 KB, still fit 8 warps x 2 stages in 227 KB).
+static int item_ks(int ntl, int MT, int item_bytes) {
+  const int budget = MT == 1 ? item_bytes : item_bytes * 13 / 16;
+  return std::max(1, budget / (512 * ntl + 2048));
 }
 
 void flow_plan_build(const std::vector<NatTask>& lt, void** plan_out) {
@@ -644,11 +950,40 @@ void flow_plan_build(const std::vector<NatTask>& lt, void** plan_out) {
   try {
     int maxd = -1;
     for (const NatTask& L : lt) maxd = std::max(maxd, L.depth);
-    for (int mt = 1; mt <= 2; ++mt) {
-      P->chains[mt].assign((size_t)(maxd + 1), {});
-      for (const NatTask& L : lt)
-        if (L.nt > 0) task_chains(L, mt, P->chains[mt][(size_t)L.depth], P->stage_bytes[mt]);
+    P->terms.assign((size_t)(maxd + 1), {});
+    for (const NatTask& L : lt) {
+      if (L.nt <= 0) continue;
+      if (L.ng < 1 || L.ng > NTW) throw Error{HB_ERR_UNSUPPORTED, "n-tile group larger than the accumulators"};
+      if (L.y_buf == 2) P->xh_tiles = std::max(P->xh_tiles, L.y_tile + L.nt);
+      const int ngr = (L.nt + L.ng - 1) / L.ng;
+      for (int g = 0; g < ngr; ++g) {
+        const int ntl = std::min(L.ng, L.nt - g * L.ng);
+        std::vector<WItem> ch;
+        for (const NatTerm& tm : L.terms) {
+          if (tm.ks <= 0) continue;
+          WItem w{};
+          w.f_tile = tm.f_tile + (long long)g * L.ng * tm.ks;
+          w.x_tile = tm.x_tile;
+          w.y_tile = L.y_tile + (long long)g * L.ng;
+          w.ks = (short)tm.ks;   // uncut: may exceed an item
+          w.ntl = (unsigned char)ntl;
+          w.x_buf = (unsigned char)tm.x_buf;
+          w.y_buf = (unsigned char)L.y_buf;
+          ch.push_back(w);
+        }
+        if (ch.empty()) {   // every input is empty: the group is zero
+          WItem w{};
+          w.y_tile = L.y_tile + (long long)g * L.ng;
+          w.ntl = (unsigned char)ntl;
+          w.y_buf = (unsigned char)L.y_buf;
+          ch.push_back(w);
+        }
+        P->terms[(size_t)L.depth].push_back(std::move(ch));
+      }
     }
+    for (const NatTask& L : lt)
+      for (const NatTerm& tm : L.terms)
+        if (tm.ks > 32767) throw Error{HB_ERR_UNSUPPORTED, "a factor block with more than 262136 inputs"};
   } catch (...) {
     delete P;
     throw;
@@ -656,132 +991,456 @@ void flow_plan_build(const std::vector<NatTask>& lt, void** plan_out) {
   *plan_out = P;
 }
 
-static void free_streams(std::vector<DepthStreams>& ss) {
-  for (DepthStreams& d : ss) {
-    dev_free(d.d_items);
-    dev_free(d.d_off);
+// The chains of one term chain cut for (MT, item bytes): each term's
+// k-steps in runs of at most item_ks; the first item zeroes the
+// accumulators, the last stores them.
+static void cut_chain(const std::vector<WItem>& tc, int MT, int item_bytes, std::vector<WItem>& out,
+                      int& stage_bytes) {
+  const size_t first = out.size();
+  for (const WItem& t : tc) {
+    if (t.ks == 0) {
+      out.push_back(t);
+      continue;
+    }
+    const int kc = item_ks(t.ntl, MT, item_bytes);
+    for (int k0 = 0; k0 < t.ks; k0 += kc) {
+      WItem w = t;
+      w.f_tile = t.f_tile + (long long)k0 * t.ntl;
+      w.x_tile = t.x_tile + k0;
+      w.ks = (short)std::min(kc, (int)t.ks - k0);
+      w.flags = 0;
+      out.push_back(w);
+      stage_bytes = std::max(stage_bytes, (int)t.ntl * (int)w.ks * 512 + (int)w.ks * MT * 1024);
+    }
   }
-  ss.clear();
+  out[first].flags |= 1;
+  out.back().flags |= 2;
+}
+
+static ChainSet& chain_set(FlowPlan* P, int MT, int item_bytes) {
+  auto key = std::make_pair(MT, item_bytes);
+  auto it = P->sets.find(key);
+  if (it != P->sets.end()) return it->second;
+  ChainSet cs;
+  cs.by_depth.assign(P->terms.size(), {});
+  for (size_t d = 0; d < P->terms.size(); ++d)
+    for (const auto& tc : P->terms[d]) {
+      std::vector<WItem> ch;
+      cut_chain(tc, MT, item_bytes, ch, cs.stage_bytes);
+      cs.by_depth[d].push_back(std::move(ch));
+    }
+  return P->sets.emplace(key, std::move(cs)).first->second;
+}
+
+static void free_streams(DepthStreams& d) {
+  dev_free(d.d_items);
+  dev_free(d.d_off);
+  d = DepthStreams{};
+}
+
+static void free_set(ChainSet& cs) {
+  for (DepthStreams& d : cs.depth_streams) free_streams(d);
+  cs.depth_streams.clear();
+  cs.depth_grid = 0;
+  for (auto& kv : cs.flow_streams) free_streams(kv.second);
+  cs.flow_streams.clear();
+  cs.flow_grid = 0;
 }
 
 void flow_plan_free(void* plan) {
   FlowPlan* P = static_cast<FlowPlan*>(plan);
   if (!P) return;
-  for (auto& ss : P->streams) free_streams(ss);
+  for (auto& kv : P->sets) free_set(kv.second);
   delete P;
 }
 
-int flow_plan_depths(const void* plan) { return (int)static_cast<const FlowPlan*>(plan)->chains[1].size(); }
+int flow_plan_depths(const void* plan) { return (int)static_cast<const FlowPlan*>(plan)->terms.size(); }
 
-// Deal every depth's chains over grid x NWARP warp streams: longest chain
-// (in factor tiles, plus a fixed cost per item) first, to the stream with
-// the least work so far.
-static void build_streams(FlowPlan* P, int grid, int MT) {
-  std::vector<DepthStreams>& out = P->streams[MT];
-  free_streams(out);
+static long long chain_cost(const std::vector<WItem>& ch) {
+  long long w = 0;
+  for (const WItem& it : ch) w += (long long)it.ntl * std::max<int>(1, it.ks) + 4;
+  return w;
+}
+
+static DepthStreams upload_streams(const std::vector<std::vector<const std::vector<WItem>*>>& per, int grid) {
+  std::vector<WItem> items;
+  std::vector<long long> off;
+  size_t total = 0;
+  for (const auto& s : per)
+    for (const auto* c : s) total += c->size();
+  items.reserve(total);
+  for (const auto& s : per) {
+    off.push_back((long long)items.size());
+    for (const auto* c : s) items.insert(items.end(), c->begin(), c->end());
+  }
+  off.push_back((long long)items.size());
+  DepthStreams ds;
+  ds.grid = grid;
+  ds.d_items = upload(items);
+  try {
+    ds.d_off = upload(off);
+  } catch (...) {
+    dev_free(ds.d_items);
+    throw;
+  }
+  HB_CUDA(cudaDeviceSynchronize());
+  return ds;
+}
+
+// Mode 0: deal every depth's chains over grid x NWARP warp streams, longest
+// chain (in factor tiles, plus a fixed cost per item) first, to the stream
+// with the least work so far.
+static void build_depth_streams(ChainSet& cs, int grid) {
+  for (DepthStreams& d : cs.depth_streams) free_streams(d);
+  cs.depth_streams.clear();
   const int ns = grid * NWARP;
-  for (const auto& chains : P->chains[MT]) {
-    DepthStreams ds;
+  for (const auto& chains : cs.by_depth) {
     if (chains.empty()) {
-      out.push_back(ds);
+      cs.depth_streams.push_back(DepthStreams{});
       continue;
     }
     std::vector<long long> cost(chains.size());
-    for (size_t c = 0; c < chains.size(); ++c) {
-      long long w = 0;
-      for (const WItem& it : chains[c]) w += (long long)it.ntl * std::max<int>(1, it.ks) + 4;
-      cost[c] = w;
-    }
+    for (size_t c = 0; c < chains.size(); ++c) cost[c] = chain_cost(chains[c]);
     std::vector<size_t> order(chains.size());
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
     using Load = std::pair<long long, int>;
     std::priority_queue<Load, std::vector<Load>, std::greater<Load>> pq;
     for (int s = 0; s < ns; ++s) pq.push({0, s});
-    std::vector<std::vector<size_t>> per((size_t)ns);
+    std::vector<std::vector<const std::vector<WItem>*>> per((size_t)ns);
     for (size_t c : order) {
       Load l = pq.top();
       pq.pop();
-      per[(size_t)l.second].push_back(c);
+      per[(size_t)l.second].push_back(&chains[c]);
       l.first += cost[c];
       pq.push(l);
     }
-    std::vector<WItem> items;
-    std::vector<long long> off;
-    for (int s = 0; s < ns; ++s) {
-      off.push_back((long long)items.size());
-      for (size_t c : per[(size_t)s]) items.insert(items.end(), chains[c].begin(), chains[c].end());
-    }
-    off.push_back((long long)items.size());
-    ds.grid = grid;
-    ds.d_items = upload(items);
-    ds.d_off = upload(off);
-    out.push_back(ds);
+    cs.depth_streams.push_back(upload_streams(per, grid));
   }
-  HB_CUDA(cudaDeviceSynchronize());
-  P->grid[MT] = grid;
+  cs.depth_grid = grid;
+}
+
+// Mode 1: one stream set over all depths, placed by simulating the schedule.
+// Chain costs as above; item k of a chain starts at (chain start + the cost
+// of the chain's items before it), and must not start before every chain
+// writing an xh row tile it reads has finished plus `slack` (time for the
+// producer to publish and for this warp's prefetch to see it); the gather,
+// which every warp runs first, counts as finished at a fixed time.  Chains
+// are taken in order of their ready time and put on the stream that frees
+// first; start = max(stream free, ready), finish = start + cost.  Each
+// stream therefore runs its items in increasing simulated start time, and
+// every producer's last item starts strictly before any item that reads
+// its output - the order the kernel's deadlock freedom rests on.
+static void build_flow_streams(ChainSet& cs, int grid, int slack, long long xh_tiles, long long nv_tiles, int MT) {
+  auto old = cs.flow_streams.find(slack);
+  if (old != cs.flow_streams.end()) {
+    free_streams(old->second);
+    cs.flow_streams.erase(old);
+  }
+  const int ns = grid * NWARP;
+  std::vector<const std::vector<WItem>*> ch;
+  for (const auto& chains : cs.by_depth)
+    for (const auto& c : chains) ch.push_back(&c);
+  const size_t nc = ch.size();
+  std::vector<long long> cost(nc);
+  for (size_t c = 0; c < nc; ++c) cost[c] = chain_cost(*ch[c]);
+  // producer of every xh row tile
+  std::vector<int> prod((size_t)std::max<long long>(xh_tiles, 1), -1);
+  for (size_t c = 0; c < nc; ++c) {
+    const WItem& w = ch[c]->back();
+    if (w.y_buf == 2)
+      for (int j = 0; j < w.ntl; ++j) prod[(size_t)(w.y_tile + j)] = (int)c;
+  }
+  // producers of every chain with the smallest prefix cost of an item that
+  // reads them; consumers as CSR of (chain, prefix)
+  std::vector<int> npend(nc, 0);
+  std::vector<std::vector<std::pair<int, long long>>> prods(nc);
+  for (size_t c = 0; c < nc; ++c) {
+    auto& ps = prods[c];
+    long long prefix = 0;
+    for (const WItem& w : *ch[c]) {
+      if (w.x_buf == 2)
+        for (int j = 0; j < w.ks; ++j) {
+          const int p = prod[(size_t)(w.x_tile + j)];
+          if (p < 0) throw Error{HB_ERR_STATE, "a chain reads a skeleton row tile no chain writes"};
+          ps.push_back({p, prefix});
+        }
+      prefix += (long long)w.ntl * std::max<int>(1, w.ks) + 4;
+    }
+    std::sort(ps.begin(), ps.end());   // by producer, smallest prefix first
+    size_t m = 0;
+    for (size_t q = 0; q < ps.size(); ++q)
+      if (m == 0 || ps[q].first != ps[m - 1].first) ps[m++] = ps[q];
+    ps.resize(m);
+    npend[c] = (int)m;
+  }
+  std::vector<long long> cons_off(nc + 1, 0);
+  for (size_t c = 0; c < nc; ++c)
+    for (const auto& pp : prods[c]) ++cons_off[(size_t)pp.first + 1];
+  for (size_t c = 0; c < nc; ++c) cons_off[c + 1] += cons_off[c];
+  std::vector<std::pair<int, long long>> cons((size_t)cons_off[nc]);
+  {
+    std::vector<long long> fill(cons_off.begin(), cons_off.end() - 1);
+    for (size_t c = 0; c < nc; ++c)
+      for (const auto& pp : prods[c]) cons[(size_t)fill[(size_t)pp.first]++] = {(int)c, pp.second};
+  }
+  std::vector<std::vector<std::pair<int, long long>>>().swap(prods);
+  const long long gather_done = 4LL * MT * ((nv_tiles + ns - 1) / ns);
+  std::vector<long long> ready(nc, gather_done);
+  using Ev = std::pair<long long, int>;   // (ready, chain)
+  std::priority_queue<Ev, std::vector<Ev>, std::greater<Ev>> rq;
+  for (size_t c = 0; c < nc; ++c)
+    if (npend[c] == 0) rq.push({ready[c], (int)c});
+  using Load = std::pair<long long, int>;   // (free at, stream)
+  std::priority_queue<Load, std::vector<Load>, std::greater<Load>> sq;
+  for (int s = 0; s < ns; ++s) sq.push({gather_done, s});
+  std::vector<std::vector<const std::vector<WItem>*>> per((size_t)ns);
+  size_t placed = 0;
+  while (!rq.empty()) {
+    const Ev e = rq.top();
+    rq.pop();
+    Load l = sq.top();
+    sq.pop();
+    const long long start = std::max(l.first, e.first);
+    const long long fin = start + cost[(size_t)e.second];
+    per[(size_t)l.second].push_back(ch[(size_t)e.second]);
+    l.first = fin;
+    sq.push(l);
+    ++placed;
+    for (long long q = cons_off[(size_t)e.second]; q < cons_off[(size_t)e.second + 1]; ++q) {
+      const int c = cons[(size_t)q].first;
+      ready[(size_t)c] = std::max(ready[(size_t)c], fin + slack - cons[(size_t)q].second);
+      if (--npend[(size_t)c] == 0) rq.push({ready[(size_t)c], c});
+    }
+  }
+  if (placed != nc) throw Error{HB_ERR_STATE, "the chain dependencies have a cycle"};
+  cs.flow_streams[slack] = upload_streams(per, grid);
+  cs.flow_grid = grid;
 }
 
 template <int MT>
-static void launch_depths(FlowPlan* P, const uint4* F, uint4* x, uint4* xh, double2* u, const long long* pperm,
-                          long long Nv, int R, int* err, long long budget, bool selftest, cudaStream_t st,
-                          const std::function<void(int, bool)>& timer) {
-  auto k = bf_step_kernel<MT>;
-  LaunchShape& L = P->shape[MT];
-  if (!L.ready) {
-    // once per plan and m-tile count: stages, shared memory, grid (then the streams)
-    int dev = 0, nsm = 0, optin = 0;
-    HB_CUDA(cudaGetDevice(&dev));
-    HB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    HB_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    cudaFuncAttributes fa{};
-    HB_CUDA(cudaFuncGetAttributes(&fa, k));
-    L.stage = P->stage_bytes[MT];
-    const int avail = optin - (int)fa.sharedSizeBytes;
-    L.stages = std::min(MAX_STAGES, avail / (NWARP * L.stage));
-    if (L.stages < 2) throw Error{HB_ERR_UNSUPPORTED, "step kernel stages do not fit in shared memory"};
-    L.smem = (size_t)NWARP * L.stages * L.stage;
-    // the kernel may take any size up to the opt-in limit (both directions' plans share it)
-    HB_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, avail));
-    int per_sm = 0;
-    HB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NWARP * 32, L.smem));
-    if (per_sm < 1) throw Error{HB_ERR_UNSUPPORTED, "step kernel does not fit on an SM"};
-    L.grid = nsm * per_sm;
-    L.ready = true;
-  }
-  if (P->grid[MT] != L.grid) build_streams(P, L.grid, MT);
-  bool first = true;   // the timer brackets all depth launches (PDL stays intact)
-  for (int d = 0; d < (int)P->streams[MT].size(); ++d) {
-    const DepthStreams& ds = P->streams[MT][(size_t)d];
-    if (ds.grid == 0) continue;
-    StepArgs args{ds.d_items, ds.d_off, F, x, xh, u, pperm, Nv, R, L.stages, L.stage, budget, err,
-                  selftest ? 1 : 0};
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(ds.grid);
-    cfg.blockDim = dim3(NWARP * 32);
-    cfg.dynamicSmemBytes = L.smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    if (first) timer(0, true);
-    first = false;
-    HB_CUDA(cudaLaunchKernelEx(&cfg, k, args));
-  }
-  if (!first) timer(0, false);
+static void set_shape(FlowPlan* P, LaunchShape& L, int mode, int item_bytes, int pub, int slack) {
+  int dev = 0, nsm = 0, optin = 0;
+  HB_CUDA(cudaGetDevice(&dev));
+  HB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  HB_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  ChainSet& cs = chain_set(P, MT, item_bytes);
+  cudaFuncAttributes fa{};
+  const void* k = mode == 0 ? (const void*)bf_step_kernel<MT> : (const void*)bf_flow_kernel<MT>;
+  HB_CUDA(cudaFuncGetAttributes(&fa, k));
+  L.mode = mode;
+  L.item_bytes = item_bytes;
+  L.pub = pub;
+  L.slack = slack;
+  L.stage = cs.stage_bytes;
+  const int avail = optin - (int)fa.sharedSizeBytes;
+  L.stages = std::min(MAX_STAGES, avail / (NWARP * L.stage));
+  if (L.stages < 2) throw Error{HB_ERR_UNSUPPORTED, "step kernel stages do not fit in shared memory"};
+  L.smem = (size_t)NWARP * L.stages * L.stage;
+  // the kernel may take any size up to the opt-in limit (both directions' plans share it)
+  HB_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, avail));
+  int per_sm = 0;
+  HB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NWARP * 32, L.smem));
+  if (per_sm < 1) throw Error{HB_ERR_UNSUPPORTED, "step kernel does not fit on an SM"};
+  L.grid = nsm * per_sm;
+  L.ready = true;
 }
 
-void flow_launch(void* plan, const uint4* F, uint4* x, uint4* xh, double2* u, const long long* pperm, long long Nv,
-                 int R, int* err, long long budget_cycles, bool selftest, cudaStream_t st,
+struct LaunchCtx {
+  const uint4* F;
+  const double2* s;
+  double scale;
+  uint4* x;
+  uint4* xh;
+  double2* u;
+  const long long* pperm;
+  long long Nv, nv_tiles;
+  int R;
+  unsigned* flags;
+  unsigned* epoch;
+  int* err;
+  long long budget;
+  bool selftest;
+  cudaStream_t st;
+};
+
+template <int MT>
+static void launch_shape(FlowPlan* P, const LaunchShape& L, const LaunchCtx& c,
+                         const std::function<void(int, bool)>& timer) {
+  ChainSet& cs = chain_set(P, MT, L.item_bytes);
+  if (L.mode == 0) {
+    gather_native(c.s, c.pperm, c.x, c.nv_tiles, c.Nv, c.R, MT, c.scale, c.st);
+    if (cs.depth_grid != L.grid) build_depth_streams(cs, L.grid);
+    bool first = true;   // the timer brackets all depth launches (PDL stays intact)
+    for (const DepthStreams& ds : cs.depth_streams) {
+      if (ds.grid == 0) continue;
+      StepArgs args{ds.d_items, ds.d_off, c.F, c.x, c.xh, c.u, c.pperm, c.Nv, c.R, L.stages, L.stage, c.budget,
+                    c.err, c.selftest ? 1 : 0};
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(ds.grid);
+      cfg.blockDim = dim3(NWARP * 32);
+      cfg.dynamicSmemBytes = L.smem;
+      cfg.stream = c.st;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      attr[0].val.programmaticStreamSerializationAllowed = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      if (first) timer(0, true);
+      first = false;
+      HB_CUDA(cudaLaunchKernelEx(&cfg, bf_step_kernel<MT>, args));
+    }
+    if (!first) timer(0, false);
+    return;
+  }
+  if (cs.flow_grid != L.grid) {
+    for (auto& kv : cs.flow_streams) free_streams(kv.second);
+    cs.flow_streams.clear();
+  }
+  if (!cs.flow_streams.count(L.slack)) build_flow_streams(cs, L.grid, L.slack, P->xh_tiles, c.nv_tiles, MT);
+  const DepthStreams& fs = cs.flow_streams[L.slack];
+  FlowArgs fa{};
+  fa.a = StepArgs{fs.d_items, fs.d_off, c.F, c.x, c.xh, c.u, c.pperm, c.Nv, c.R,
+                  L.stages, L.stage, c.budget, c.err, c.selftest ? 1 : 0};
+  fa.s = c.s;
+  fa.scale = c.scale;
+  fa.nv_tiles = c.nv_tiles;
+  fa.flags = c.flags;
+  fa.epoch = c.epoch;
+  fa.pub_batch = L.pub;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(L.grid);
+  cfg.blockDim = dim3(NWARP * 32);
+  cfg.dynamicSmemBytes = L.smem;
+  cfg.stream = c.st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;   // every CTA resident: chains wait on one another
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  timer(0, true);
+  HB_CUDA(cudaLaunchKernelEx(&cfg, bf_flow_kernel<MT>, fa));
+  timer(0, false);
+}
+
+// The autotuner: time every candidate shape (each a full apply of these
+// right-hand sides, one untimed run then the best of three, CUDA events on
+// the caller's stream) and keep the fastest.  Candidates: one launch per
+// depth at 16 KB and 8 KB items; the dataflow launch at 16 KB and 8 KB items
+// with 1 and 4 chains per publication.  Only the winner's streams are kept.
+template <int MT>
+static void autotune(FlowPlan* P, LaunchShape& L, const LaunchCtx& c) {
+  struct Cand {
+    int mode, item_bytes, pub, slack;
+  };
+  const Cand cands[] = {{0, 16384, 1, 0},  {0, 8192, 1, 0},   {1, 16384, 1, 16}, {1, 16384, 1, 48},
+                        {1, 16384, 1, 128}, {1, 16384, 4, 48}, {1, 8192, 1, 16},  {1, 8192, 1, 48},
+                        {1, 8192, 1, 128}};
+  cudaEvent_t e0, e1;
+  HB_CUDA(cudaEventCreate(&e0));
+  HB_CUDA(cudaEventCreate(&e1));
+  auto none = [](int, bool) {};
+  double best = 1e30;
+  LaunchShape win;
+  int timed = 0;
+  try {
+    for (const Cand& k : cands) {
+      LaunchShape T;
+      try {
+        set_shape<MT>(P, T, k.mode, k.item_bytes, k.pub, k.slack);
+      } catch (const Error&) {
+        continue;   // does not fit: not a candidate
+      }
+      launch_shape<MT>(P, T, c, none);
+      float ms = 1e30f;
+      for (int rep = 0; rep < 3; ++rep) {
+        HB_CUDA(cudaEventRecord(e0, c.st));
+        launch_shape<MT>(P, T, c, none);
+        HB_CUDA(cudaEventRecord(e1, c.st));
+        HB_CUDA(cudaEventSynchronize(e1));
+        float t = 0;
+        HB_CUDA(cudaEventElapsedTime(&t, e0, e1));
+        ms = std::min(ms, t);
+      }
+      ++timed;
+      if (ms < best) {
+        best = ms;
+        win = T;
+      }
+    }
+  } catch (...) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    throw;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!timed) throw Error{HB_ERR_UNSUPPORTED, "no launch shape fits"};
+  win.tuned_ms = best;
+  win.candidates = timed;
+  L = win;
+  // keep only the winner's chains and streams
+  for (auto it = P->sets.begin(); it != P->sets.end();) {
+    if (it->first.first == MT && it->first.second != L.item_bytes) {
+      free_set(it->second);
+      it = P->sets.erase(it);
+    } else {
+      ++it;
+    }
+  }
+  ChainSet& cs = chain_set(P, MT, L.item_bytes);
+  for (auto it = cs.flow_streams.begin(); it != cs.flow_streams.end();) {
+    if (L.mode == 0 || it->first != L.slack) {
+      free_streams(it->second);
+      it = cs.flow_streams.erase(it);
+    } else {
+      ++it;
+    }
+  }
+  if (L.mode == 1) {
+    for (DepthStreams& d : cs.depth_streams) free_streams(d);
+    cs.depth_streams.clear();
+    cs.depth_grid = 0;
+  }
+}
+
+template <int MT>
+static void run_mt(FlowPlan* P, const LaunchCtx& c, int tune, const std::function<void(int, bool)>& timer) {
+  LaunchShape& L = P->shape[MT];
+  if (!L.ready) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    HB_CUDA(cudaStreamIsCapturing(c.st, &cap));
+    if (tune == 1 && cap == cudaStreamCaptureStatusNone) autotune<MT>(P, L, c);
+    else if (tune == 2) set_shape<MT>(P, L, 1, ITEM_BYTES, 1, 48);
+    else set_shape<MT>(P, L, 0, ITEM_BYTES, 1, 0);
+  }
+  launch_shape<MT>(P, L, c, timer);
+}
+
+void flow_launch(void* plan, const uint4* F, const double2* s, double scale, uint4* x, uint4* xh, double2* u,
+                 const long long* pperm, long long Nv, long long nv_tiles, int R, unsigned* flags, unsigned* epoch,
+                 int* err, long long budget_cycles, bool selftest, int autotune_on, cudaStream_t st,
                  const std::function<void(int, bool)>& timer) {
   FlowPlan* P = static_cast<FlowPlan*>(plan);
-  if (P->chains[1].empty()) return;
+  if (P->terms.empty()) return;
   const int MT = (R + 15) / 16;
-  if (MT == 1) launch_depths<1>(P, F, x, xh, u, pperm, Nv, R, err, budget_cycles, selftest, st, timer);
-  else if (MT == 2) launch_depths<2>(P, F, x, xh, u, pperm, Nv, R, err, budget_cycles, selftest, st, timer);
+  const LaunchCtx c{F, s, scale, x, xh, u, pperm, Nv, nv_tiles, R, flags, epoch, err, budget_cycles, selftest, st};
+  if (MT == 1) run_mt<1>(P, c, autotune_on, timer);
+  else if (MT == 2) run_mt<2>(P, c, autotune_on, timer);
   else throw Error{HB_ERR_UNSUPPORTED, "the mixed apply takes 1 or 2 m-tiles of 16 right-hand sides per pass"};
+}
+
+void flow_shape(const void* plan, int MT, int* mode, int* item_bytes, int* stages, int* pub, int* slack,
+                double* tuned_ms, int* candidates) {
+  const FlowPlan* P = static_cast<const FlowPlan*>(plan);
+  const LaunchShape& L = P->shape[MT];
+  *mode = L.ready ? L.mode : -1;
+  *item_bytes = L.item_bytes;
+  *stages = L.stages;
+  *pub = L.pub;
+  *slack = L.slack;
+  *tuned_ms = L.tuned_ms;
+  *candidates = L.candidates;
 }
 
 }  // namespace hb

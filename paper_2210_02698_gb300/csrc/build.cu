@@ -615,7 +615,10 @@ static void make_plans(hb_ctx* c, std::vector<Butterfly>& bfs, const std::vector
           const int sz = leaf_size(t);
           NatTask o = task(c->leaf_tile[(size_t)t], tiles8(sz), Lmax + 1, 1);
           o.terms.push_back(term(nat(leaf_off[(size_t)t], sz, sz, 0, sz, 0), c->leaf_tile[(size_t)t], tiles8(sz), 0));
-          for (int l = 1; l <= Lv; ++l) {
+          // terms in the order their inputs are produced (HODBF level Lv,
+          // whose K^L input is written at depth 0, first): a dataflow launch
+          // can start the leaf outputs before the deepest butterflies finish
+          for (int l = Lv; l >= 1; --l) {
             const long long oi = t >> (Lv - l);
             const Butterfly& b = bfs[(size_t)bf_of_o(l, oi)];
             const long long i = t - (oi << b.L);
@@ -665,7 +668,7 @@ static void make_plans(hb_ctx* c, std::vector<Butterfly>& bfs, const std::vector
           const int sz = leaf_size(t);
           NatTask o = task(c->leaf_tile[(size_t)t], tiles8(sz), Lmax + 1, 1);
           o.terms.push_back(term(nat(leaf_off[(size_t)t], sz, sz, 0, sz, 0), c->leaf_tile[(size_t)t], tiles8(sz), 0));
-          for (int l = 1; l <= Lv; ++l) {
+          for (int l = Lv; l >= 1; --l) {   // inputs in the order they are produced (as above)
             const long long si = t >> (Lv - l);
             const Butterfly& b = bfs[(size_t)bf_of_s(l, si)];
             const long long j = t - (si << b.L);
@@ -690,8 +693,9 @@ static void make_plans(hb_ctx* c, std::vector<Butterfly>& bfs, const std::vector
   c->stats.factor_bytes_fp64 = c->n_factor * (long long)sizeof(double2);
   c->stats.factor_bytes_mixed = c->nat_tiles[0] * 512;
   c->stats.skeleton_rows = c->xh_rows;
-  // mixed-precision apply of up to 32 right-hand sides: the gather and one
-  // step launch per dependency depth (the last one writes u)
+  // mixed-precision apply of up to 32 right-hand sides in the default
+  // shape: the gather and one step launch per dependency depth (the last one
+  // writes u)
   c->stats.apply_launches = 1 + flow_plan_depths(c->flow_plan[0]);
 }
 

@@ -252,6 +252,10 @@ struct hb_ctx {
   // mixed apply scratch (native layout, up to 32 right-hand sides)
   uint4* d_mx = nullptr;
   uint4* d_mxh = nullptr;
+  // readiness flags of the dataflow launch (x row tiles, then xh row tiles)
+  // and its launch counter ([0] launches completed, [1] CTAs done)
+  unsigned* d_flags = nullptr;
+  unsigned* d_epoch = nullptr;
   // dense apply: per-split partial sums when source lines are split over CTAs
   double2* d_dense_part = nullptr;
   size_t dense_part_cap = 0;
@@ -304,10 +308,15 @@ void id_batch_noalloc(int count, const int* m, const int* n, const long long* a_
 void flow_plan_build(const std::vector<NatTask>& tasks, void** plan_out);
 void flow_plan_free(void* plan);
 int flow_plan_depths(const void* plan);
-// R <= 32 right-hand sides; the last depth writes u (natural order) itself
-void flow_launch(void* plan, const uint4* F, uint4* x, uint4* xh, double2* u, const long long* pperm, long long Nv,
-                 int R, int* err, long long budget_cycles, bool selftest, cudaStream_t st,
+// R <= 32 right-hand sides: gather of s (scaled), every depth, the last
+// depth writing u (natural order) itself; one launch per depth or one
+// persistent dataflow launch (flags / epoch: its readiness words)
+void flow_launch(void* plan, const uint4* F, const double2* s, double scale, uint4* x, uint4* xh, double2* u,
+                 const long long* pperm, long long Nv, long long nv_tiles, int R, unsigned* flags, unsigned* epoch,
+                 int* err, long long budget_cycles, bool selftest, int autotune_on, cudaStream_t st,
                  const std::function<void(int, bool)>& timer);
+void flow_shape(const void* plan, int MT, int* mode, int* item_bytes, int* stages, int* pub, int* slack,
+                double* tuned_ms, int* candidates);
 void nat_convert(const double2* F64, const std::vector<NatBlock>& blocks, uint4* out, cudaStream_t st);
 void gather_native(const double2* s, const long long* pperm, uint4* x, long long nv_tiles, long long Nv, int R,
                    int MT, double scale, cudaStream_t st);

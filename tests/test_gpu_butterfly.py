@@ -95,18 +95,29 @@ def test_tight_tolerance_reproduces_dense():
 
 
 def test_grad256_fullsize_sampled_rows():
-    """The 256^2, 16-RHS workload in the configuration the benchmark times."""
+    """The 256^2, 16-RHS workload in the configuration the benchmark times:
+    128 seeded rows of the forward apply and 64 seeded columns of the
+    adjoint against the dense oracle, FP64 (1e-5) and mixed (1e-4), each
+    right-hand side on its own as well as all together."""
     from oracle import dense
     from paper_2210_02698_gb300 import binding
     w = W.WORKLOADS["grad256"]
-    og, gp = oracle_op(w), gpu_op(w, precision=binding.HB_FP64)
+    og, gp = oracle_op(w), gpu_op(w, precision=binding.HB_FP64, autotune=1)
     gp.build()
     s = W.workload_sources(w)
-    rows = W.sample_rows(w.grid.Nv, 24, 99)
+    rows = W.sample_rows(w.grid.Nv, 128, 99)
+    cols = W.sample_rows(w.grid.Nv, 64, 98)
     want = dense.apply(og, s, rows=rows, chunk=8192)
-    assert rel_l2(_apply(gp, s)[rows], want) < 1e-5
-    gp.set_precision(binding.HB_MIXED_BF16X3)
-    assert rel_l2(_apply(gp, s)[rows], want) < 1e-4
+    wantA = dense.adjoint(og, s, cols=cols, chunk=8192)
+
+    def worst_col(a, b):
+        return float(np.max(np.linalg.norm(a - b, axis=0) / np.linalg.norm(b, axis=0)))
+    for prec, tol in ((binding.HB_FP64, 1e-5), (binding.HB_MIXED_BF16X3, 1e-4)):
+        gp.set_precision(prec)
+        got, gotA = _apply(gp, s)[rows], _apply(gp, s, True)[cols]
+        assert rel_l2(got, want) < tol and worst_col(got, want) < tol
+        assert rel_l2(gotA, wantA) < tol and worst_col(gotA, wantA) < tol
+    gp.close()
 
 
 def test_autograd_gradient_matches_finite_differences():

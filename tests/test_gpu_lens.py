@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 from paper_2210_02698_gb300 import workloads as W
-from tests._common import from_dev, gpu_op, oracle_op, rel_l2, to_dev
+from tests._common import from_dev, gpu_op, oracle_dense_rows, oracle_op, rel_l2, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -50,7 +50,7 @@ def test_lens_small_grid_vs_dense_oracle():
 @pytest.mark.slow
 def test_lens1024_fullsize_sampled_rows():
     """1024^2 cells, w = 2 pi 128, 64 mixed right-hand sides (two passes of
-    32 in the mixed apply); 8 seeded rows against the dense oracle."""
+    32 in the mixed apply); 24 seeded rows against the dense oracle."""
     import torch
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
@@ -58,8 +58,8 @@ def test_lens1024_fullsize_sampled_rows():
     from paper_2210_02698_gb300 import binding
     w = W.WORKLOADS["lens1024"]
     s = W.workload_sources(w)
-    rows = W.sample_rows(w.grid.Nv, 8, 4242)
-    want = dense.apply(oracle_op(w), s, rows=rows, chunk=8192)
+    rows = W.sample_rows(w.grid.Nv, 24, 4242)
+    want = oracle_dense_rows(w, s, rows)
     gp = gpu_op(w, precision=binding.HB_MIXED_BF16X3)
     gp.build()
     s_dev = to_dev(s)

@@ -1,6 +1,7 @@
 """Failure detection of the mixed apply without a GPU fault.  With the wait
-self-test on, the first warp of every step launch also waits - through the
-same bounded wait as the data waits - on an mbarrier that nothing completes;
+self-test on, the first warp of every step launch (of the dataflow launch:
+after its stream) also waits - through the same bounded wait as the data
+waits - on an mbarrier that nothing completes;
 with a short budget the wait runs out, the mapped error word is set and the
 next apply reports HB_ERR_TIMEOUT.  The apply itself completes, and the CUDA
 context stays usable: the same handle, self-test off, matches the oracle."""
@@ -11,7 +12,8 @@ from tests._common import gpu_op, oracle_op, rel_l2, to_dev, from_dev
 
 
 @pytest.mark.gpu
-def test_wait_that_runs_out_is_reported_and_context_survives():
+@pytest.mark.parametrize("shape", [0, 2])   # per-depth launches; the persistent dataflow launch
+def test_wait_that_runs_out_is_reported_and_context_survives(shape):
     import torch
     from paper_2210_02698_gb300 import binding
     from oracle import dense
@@ -22,7 +24,7 @@ def test_wait_that_runs_out_is_reported_and_context_survives():
     u_dev = torch.empty_like(s_dev)
 
     # about 0.5 ms of SM cycles per wait: the data waits finish long before
-    op = gpu_op(w, precision=binding.HB_MIXED_BF16X3, barrier_cycles=1 << 20)
+    op = gpu_op(w, precision=binding.HB_MIXED_BF16X3, barrier_cycles=1 << 20, autotune=shape)
     op.build()
     op.set_wait_selftest(True)
     op.apply(s_dev, u_dev, s.shape[1])

@@ -273,3 +273,22 @@ def test_host_point_proxy_rows_match_oracle_prototype(L):
                 want = cb.Butterfly._proxy(obj, t0, t1, seeds)
                 got = binding.host_point_proxy_rows(rows, t0, t1, cols[seeds], chi, radius)
                 assert np.array_equal(got, want), (lvl, chi, radius)
+
+
+def test_binding_methods_marshal_through_a_null_handle(L):
+    """The binding's handle methods reach the library with well-formed
+    arguments: on an Operator whose handle is NULL each call comes back as
+    HB_ERR_ARG (null handle) rather than a ctypes argument error."""
+    from paper_2210_02698_gb300 import binding
+    op = binding.Operator.__new__(binding.Operator)
+    op.handle = None
+    calls = [lambda: op.launch_shape(False, 1), lambda: op.launch_shape(True, 2),
+             lambda: op.record_id_blocks(4), lambda: op.recorded_id_blocks(), lambda: op.info(),
+             lambda: op.tree_perm() if hasattr(op, "Nv") else op._call("hb_tree_perm", None),
+             lambda: op.set_kernel_timing(True), lambda: op.set_precision(binding.HB_FP64)]
+    for f in calls:
+        with pytest.raises(binding.HBError) as e:
+            f()
+        assert e.value.status == binding.HB_ERR_ARG
+    v = C.c_double()
+    assert L.hb_fp64_fma_peak(None, None) == binding.HB_ERR_ARG
