@@ -258,7 +258,7 @@ def run_ours(args):
     build.build()
     w = W.WORKLOADS[args.workload]
     tab = load_tables(w)
-    tune = {"tuned": 1, "depth": 0, "dataflow": 2}[args.shape]
+    tune = {"tuned": 1, "depth": 0, "dataflow": 2, "tc_leaf": 3}[args.shape]
     op = binding.Operator(w.N, tab["nodes"], tab["tau2"], tab["v0"], tab["v1"], w.n_cells(), w.omega,
                           eps=w.eps, leaf=w.leaf, chi=w.chi, precision=binding.HB_MIXED_BF16X3, autotune=tune)
     t0 = time.perf_counter()
@@ -472,11 +472,15 @@ def run_ours(args):
         # pairs), and the input: read once as FP64 complex by the dataflow
         # launch, which gathers it itself, or read once as the 8-byte pairs the
         # separate gather wrote, when the step kernels run one launch per depth
+        # (the tensor-core leaf shape's gather also writes x in the operand
+        # layout the leaf kernel reads: not algorithmic, not counted)
         in_bytes = 16 if shape["mode"] == 1 else 8
         alg_bytes = fac_bytes + Nv * R * (in_bytes + 16) + 2 * info["skeleton_rows"] * R * 8
-        kernel_what = ("one persistent dataflow launch per pass of 32 right-hand sides (gather and every "
-                       "butterfly level)" if shape["mode"] == 1 else
-                       "butterfly step kernels of one apply (one launch per dependency depth)")
+        kernel_what = {1: "one persistent dataflow launch per pass of 32 right-hand sides (gather and every "
+                          "butterfly level)",
+                       0: "butterfly step kernels of one apply (one launch per dependency depth)",
+                       2: "butterfly step kernels of one apply (one launch per dependency depth; the leaf "
+                          "outputs on the tcgen05 tensor-core kernel)"}[shape["mode"]]
         launches = passes * (1 if shape["mode"] == 1 else 1 + info["levels"] + 1)
         achieved = alg_bytes / (step_ms * 1e-3) / 1e9
         value = Nv * R * world / (ms * 1e-3)
@@ -592,9 +596,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(W.WORKLOADS))
     ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU oracle leg (profiling runs)")
-    ap.add_argument("--shape", default="tuned", choices=["tuned", "dataflow", "depth"],
+    ap.add_argument("--shape", default="tuned", choices=["tuned", "dataflow", "depth", "tc_leaf"],
                     help="launch shape of the mixed apply: autotuned (default), the persistent dataflow "
-                         "launch, or one launch per dependency depth")
+                         "launch, one launch per dependency depth, or that with the leaf outputs on the "
+                         "tcgen05 tensor-core kernel")
     ap.add_argument("--one-core-sample", nargs=3, metavar=("WORKLOAD", "ROWS", "SEED"), help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.one_core_sample:

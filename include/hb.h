@@ -99,7 +99,9 @@ typedef struct {
  * the tuning (milliseconds to seconds, growing with N_v); under stream
  * capture no tuning happens and the default shape is used.  2 = always the
  * persistent dataflow launch (16 KB items, slack 48, one chain per
- * publication). */
+ * publication).  3 = one launch per dependency depth with the leaf outputs
+ * on the 5th-generation tensor cores (tcgen05.mma, accumulators in tensor
+ * memory; the autotuner's candidates include this shape too). */
 typedef struct {
   double eps;
   int leaf;
@@ -325,7 +327,9 @@ hb_status hb_fp64_fma_peak(double* tflops, void* stream);
  * (adjoint 0 or 1) and m-tile count (mtiles 1: up to 16 right-hand sides
  * per pass, 2: up to 32): *mode = 0 for a gather plus one launch per
  * dependency depth, 1 for one persistent dataflow launch (the gather
- * inside), -1 if no apply has run yet at that m-tile count; *item_bytes the
+ * inside), 2 for a gather plus one launch per depth with the leaf outputs
+ * on the tcgen05 tensor-core kernel, -1 if no apply has run yet at that
+ * m-tile count; *item_bytes the
  * item size the accumulation chains are cut to, *stages the shared-memory
  * ring stages per warp, *pub_batch the chains a dataflow warp publishes
  * together, *slack the dataflow placement's margin between a producer's

@@ -112,13 +112,16 @@ void free_all(hb_ctx* c) {
   for (void* p : {(void*)c->d_nodes, (void*)c->d_tab, (void*)c->d_LX, (void*)c->d_LZ, (void*)c->d_H[0],
                   (void*)c->d_H[1], (void*)c->d_ncell, (void*)c->d_self, (void*)c->d_perm, (void*)c->d_f64,
                   (void*)c->d_nat[0], (void*)c->d_nat[1], (void*)c->d_pperm, (void*)c->d_mx,
-                  (void*)c->d_mxh, c->d_x, c->d_y, (void*)c->d_dense_part, (void*)c->d_flags})
+                  (void*)c->d_mxh, c->d_x, c->d_y, (void*)c->d_dense_part, (void*)c->d_flags, (void*)c->d_mx_tc,
+                  (void*)c->d_tc[0], (void*)c->d_tc[1]})
     hb::dev_free(p);
   hb::dev_free(c->d_xh);
   hb::dev_free(c->d_tasks[0]);
   hb::dev_free(c->d_tasks[1]);
   hb::flow_plan_free(c->flow_plan[0]);
   hb::flow_plan_free(c->flow_plan[1]);
+  hb::tc_plan_free(c->tc_plan[0]);
+  hb::tc_plan_free(c->tc_plan[1]);
   hb::curve_free(c);
   if (c->h_err) cudaFreeHost(c->h_err);
 }
@@ -152,7 +155,7 @@ hb_ctx* create_ctx(const hb_grid* grid, const hb_tables* tables, double omega, c
     throw hb::arg_error("bad options (eps > 0, leaf >= 1, chi > 0, radius >= 0)");
   if (opts->precision != HB_FP64 && opts->precision != HB_MIXED_BF16X3)
     throw hb::arg_error("unknown precision %d", opts->precision);
-  if (opts->autotune < 0 || opts->autotune > 2) throw hb::arg_error("autotune must be 0, 1 or 2");
+  if (opts->autotune < 0 || opts->autotune > 3) throw hb::arg_error("autotune must be 0, 1, 2 or 3");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
     cudaGetLastError();
@@ -241,10 +244,13 @@ hb_status hb_build(hb_handle h) {
       h->d_f64 = nullptr;
       h->d_tasks[0] = h->d_tasks[1] = nullptr;
       h->d_nat[0] = h->d_nat[1] = nullptr;
+      h->d_tc[0] = h->d_tc[1] = nullptr;
       h->d_pperm = nullptr;
       for (int d = 0; d < 2; ++d) {
         hb::flow_plan_free(h->flow_plan[d]);
         h->flow_plan[d] = nullptr;
+        hb::tc_plan_free(h->tc_plan[d]);
+        h->tc_plan[d] = nullptr;
       }
       h->id_recs.clear();
       throw;

@@ -178,15 +178,17 @@ void ensure_scratch(hb_ctx* c, int nrhs, bool fp64) {
     fresh = true;
     c->d_perm = upload(c->perm);
   }
-  if (!fp64 && (!c->d_mx || !c->d_mxh || !c->d_flags)) {
-    // native vectors for two m-tiles: 2 KB per row tile, and the dataflow
-    // launch's flags (all or none: an allocation that failed half way is
-    // redone whole on the next call)
+  if (!fp64 && (!c->d_mx || !c->d_mxh || !c->d_flags || !c->d_mx_tc)) {
+    // native vectors for two m-tiles: 2 KB per row tile, x again in the
+    // tensor-core operand layout, and the dataflow launch's flags (all or
+    // none: an allocation that failed half way is redone whole on the next
+    // call)
     fresh = true;
-    for (void* p : {(void*)c->d_mx, (void*)c->d_mxh, (void*)c->d_flags}) dev_free(p);
-    c->d_mx = c->d_mxh = nullptr;
+    for (void* p : {(void*)c->d_mx, (void*)c->d_mxh, (void*)c->d_flags, (void*)c->d_mx_tc}) dev_free(p);
+    c->d_mx = c->d_mxh = c->d_mx_tc = nullptr;
     c->d_flags = c->d_epoch = nullptr;
     c->d_mx = dev_alloc<uint4>((size_t)std::max<long long>(c->nv_tiles, 1) * 128);
+    c->d_mx_tc = dev_alloc<uint4>((size_t)std::max<long long>(c->nv_tiles, 1) * 128);
     c->d_mxh = dev_alloc<uint4>((size_t)std::max<long long>(c->xh_tiles, 1) * 128);
     const size_t nflags = (size_t)(c->nv_tiles + c->xh_tiles) + 2;
     c->d_flags = dev_alloc<unsigned>(nflags);
@@ -249,8 +251,9 @@ void apply_bf(hb_ctx* c, const double2* s, double2* u, int nrhs, int adjoint, in
       // the gather and every depth (the last one writes u): one persistent
       // launch, or a gather and one launch per depth; the timer brackets the
       // step launches (with the gather inside them in the first form)
-      flow_launch(c->flow_plan[adjoint], c->d_nat[adjoint], sc, scale, c->d_mx, c->d_mxh, uc, c->d_pperm, c->Nv,
-                  c->nv_tiles, R, c->d_flags, c->d_epoch, c->d_err,
+      flow_launch(c->flow_plan[adjoint], c->tc_plan[adjoint], c->d_tc[adjoint], c->d_nat[adjoint], sc, scale,
+                  c->d_mx, c->d_mx_tc, c->d_mxh, uc, c->d_pperm, c->Nv, c->nv_tiles, R, c->d_flags, c->d_epoch,
+                  c->d_err,
                   c->opt.barrier_cycles > 0 ? c->opt.barrier_cycles : (1LL << 31), c->wait_selftest,
                   c->opt.autotune, st, [&](int, bool begin) {
                     if (begin) ts.begin(adjoint ? "bf_tc_adjoint" : "bf_tc");

@@ -58,10 +58,12 @@
 #include <cstdint>
 #include <cstring>
 #include <map>
+#include <tuple>
 #include <numeric>
 #include <queue>
 #include <vector>
 
+#include "async_copy.cuh"
 #include "hb_internal.cuh"
 
 namespace hb {
@@ -100,85 +102,12 @@ struct WItem {
 static_assert(sizeof(WItem) == 32, "item layout");
 
 // ------------------------------------------------------------ helpers ----
-__device__ __forceinline__ uint32_t bf16x2(float lo, float hi) {
-  uint32_t d;
-  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
-  return d;
-}
-
-// split-BF16 pair of the complex value (re, im)
-__device__ __forceinline__ uint2 to_pair(float re, float im) {
-  const uint32_t hi = bf16x2(re, im);
-  const float hr = __uint_as_float(hi << 16), hm = __uint_as_float(hi & 0xffff0000u);
-  return make_uint2(hi, bf16x2(re - hr, im - hm));
-}
-
 __device__ __forceinline__ void mma16816(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
   asm volatile(
       "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
       "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
       : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Wait for an mbarrier phase until the deadline (clock64 of this SM).
-__device__ __forceinline__ bool mbar_wait_until(uint64_t* bar, uint32_t parity, long long deadline) {
-  while (!mbar_try_wait(bar, parity))
-    if (clock64() > deadline) return false;
-  return true;
-}
-
-// 1D bulk copy global -> shared, completion counted on the mbarrier, with
-// an L2 cache policy.  dst, src 16-byte aligned, bytes a multiple of 16.
-__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
-                                            uint64_t policy) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], "
-      "%4;\n" ::"r"(smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
-      : "memory");
-}
-
-// L2 policies: factors stream through once per apply (evict first); the
-// vectors are written by one depth and read by the next (evict last).
-__device__ __forceinline__ uint64_t policy_evict_first() {
-  uint64_t p;
-  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-__device__ __forceinline__ uint64_t policy_evict_last() {
-  uint64_t p;
-  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-
-__device__ __forceinline__ void st_global_hint(uint4* p, const uint4& v, uint64_t policy) {
-  asm volatile("st.global.L2::cache_hint.v4.u32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "r"(v.x), "r"(v.y),
-               "r"(v.z), "r"(v.w), "l"(policy)
-               : "memory");
 }
 
 struct StepArgs {
@@ -283,6 +212,34 @@ __device__ __forceinline__ void store_tiles(uint4* Y, int ntl, int lane, const f
       uint4* o = Y + ((size_t)j * MT + mt) * 64;
       st_global_hint(o + lane, make_uint4(p0.x, p2.x, p1.x, p3.x), policy);
       st_global_hint(o + 32 + lane, make_uint4(p0.y, p2.y, p1.y, p3.y), policy);
+    }
+  }
+}
+
+// Store ntl n-tiles of the accumulators as row tiles in the operand layout
+// of the tensor-core leaf kernel (leaf_tc.cu): in the 1 KB of row tile
+// (y_tile + j, m-tile mt), the bf16 of (n = 16 c + rho, k) sits at
+// (n / 8) 64 + (n % 8) 8 + k, c = 2 q + s for part q (Re, Im) of split half s
+// (hi, lo) of right-hand side rho, k the row within the tile.  Lane (g, t)
+// holds rows 2t, 2t + 1 of right-hand sides g and g + 8 (h = 0, 1), so each
+// (c, h) is one 4-byte word per lane at word (2 c + h) 32 + lane.
+template <int MT>
+__device__ __forceinline__ void store_tiles_tc(uint4* Y, int ntl, int lane, const float (&acc)[NTW][MT][8]) {
+#pragma unroll
+  for (int j = 0; j < NTW; ++j) {
+    if (j >= ntl) break;
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt) {
+      const float* a = acc[j][mt];
+      uint32_t* o = reinterpret_cast<uint32_t*>(Y + ((size_t)j * MT + mt) * 64);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const uint2 p0 = to_pair(a[2 * h], a[2 * h + 4]), p1 = to_pair(a[2 * h + 1], a[2 * h + 5]);
+        o[(0 + h) * 32 + lane] = (p0.x & 0xffffu) | (p1.x << 16);
+        o[(2 + h) * 32 + lane] = (p0.y & 0xffffu) | (p1.y << 16);
+        o[(4 + h) * 32 + lane] = (p0.x >> 16) | (p1.x & 0xffff0000u);
+        o[(6 + h) * 32 + lane] = (p0.y >> 16) | (p1.y & 0xffff0000u);
+      }
     }
   }
 }
@@ -433,6 +390,7 @@ __global__ void __launch_bounds__(NWARP * 32, 1) bf_step_kernel(StepArgs a) {
     if (ks > 0) item_mma<MT>(st, st + ntl * ks * 32, ks, ntl, lane, acc);
     if (flags & 2) {
       if (w.y_buf == 1) store_natural<MT>(a, w.y_tile, ntl, lane, acc);
+      else if (flags & 4) store_tiles_tc<MT>(a.xh + (size_t)w.y_tile * (MT * 64), ntl, lane, acc);
       else store_tiles<MT>(a.xh + (size_t)w.y_tile * (MT * 64), ntl, lane, acc, pol_v);
     }
     // every lane's reads of stage s are done before lane 0 refills it
@@ -728,7 +686,8 @@ __global__ void __launch_bounds__(NWARP * 32, 1) bf_flow_kernel(FlowArgs f) {
       if (w.y_buf == 1) {
         store_natural<MT>(a, w.y_tile, ntl, lane, acc);
       } else {
-        store_tiles<MT>(a.xh + (size_t)w.y_tile * (MT * 64), ntl, lane, acc, pol_v);
+        if (flags & 4) store_tiles_tc<MT>(a.xh + (size_t)w.y_tile * (MT * 64), ntl, lane, acc);
+        else store_tiles<MT>(a.xh + (size_t)w.y_tile * (MT * 64), ntl, lane, acc, pol_v);
         if (npub + ntl > PUB_MAX) publish();
         if (lane < ntl) pubs[warp][npub + lane] = (int)(w.y_tile + lane);
         npub += ntl;
@@ -847,12 +806,16 @@ __device__ __forceinline__ void word_coords(long long q, int MT, long long& rt, 
 // One warp per (row tile, m-tile): lane l reads rows l & 7, right-hand sides
 // 16 mt + 4 (l >> 3) + c (c < 4) - for each c, eight lanes read one 128-byte
 // run of a column when a leaf row is contiguous in natural order - and the
-// pairs are transposed through shared memory into fragment order.
+// pairs are transposed through shared memory into fragment order.  With
+// x_tc, the tile is also written in the tensor-core operand layout (bf16 of
+// (n = 16 c + rho, row k) at (n / 8) 64 + (n % 8) 8 + k, c = 2 q + s).
 __global__ void __launch_bounds__(256) gather_native_kernel(const double2* __restrict__ s,
                                                             const long long* __restrict__ pperm,
-                                                            uint4* __restrict__ x, long long nv_tiles, long long Nv,
-                                                            int R, int MT, double scale) {
+                                                            uint4* __restrict__ x, uint4* __restrict__ x_tc,
+                                                            long long nv_tiles, long long Nv, int R, int MT,
+                                                            double scale) {
   __shared__ __align__(16) uint32_t tile[8][256];
+  __shared__ __align__(16) uint16_t ttc[8][512];
   // the first depth launch may start now and stream its factor runs; it
   // reads x only after griddepcontrol.wait, i.e. after this grid completes
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
@@ -877,18 +840,32 @@ __global__ void __launch_bounds__(256) gather_native_kernel(const double2* __res
     const uint2 p = to_pair((float)(v[c].x * scale), (float)(v[c].y * scale));
     tile[wb][dl * 4 + dj] = p.x;
     tile[wb][128 + dl * 4 + dj] = p.y;
+    if (x_tc) {
+      const uint16_t part[4] = {(uint16_t)(p.x & 0xffffu), (uint16_t)(p.y & 0xffffu), (uint16_t)(p.x >> 16),
+                                (uint16_t)(p.y >> 16)};   // (Re, hi), (Re, lo), (Im, hi), (Im, lo)
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc) {
+        const int n = 16 * cc + q;
+        ttc[wb][(n >> 3) * 64 + (n & 7) * 8 + r] = part[cc];
+      }
+    }
   }
   __syncwarp();
   uint4* out = x + (size_t)wid * 64;   // tile (rt, mt) = rt * MT + mt = wid
   out[lane] = reinterpret_cast<const uint4*>(tile[wb])[lane];
   out[32 + lane] = reinterpret_cast<const uint4*>(tile[wb])[32 + lane];
+  if (x_tc) {
+    uint4* ot = x_tc + (size_t)wid * 64;
+    ot[lane] = reinterpret_cast<const uint4*>(ttc[wb])[lane];
+    ot[32 + lane] = reinterpret_cast<const uint4*>(ttc[wb])[32 + lane];
+  }
 }
 
-void gather_native(const double2* s, const long long* pperm, uint4* x, long long nv_tiles, long long Nv, int R,
-                   int MT, double scale, cudaStream_t st) {
+void gather_native(const double2* s, const long long* pperm, uint4* x, uint4* x_tc, long long nv_tiles, long long Nv,
+                   int R, int MT, double scale, cudaStream_t st) {
   const long long warps = nv_tiles * MT;
   if (warps == 0) return;
-  gather_native_kernel<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(s, pperm, x, nv_tiles, Nv, R, MT, scale);
+  gather_native_kernel<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(s, pperm, x, x_tc, nv_tiles, Nv, R, MT, scale);
   HB_CHECK_LAUNCH();
 }
 
@@ -911,6 +888,7 @@ struct LaunchShape {
   int stage = 0, stages = 0, grid = 0;
   int pub = 2;
   int slack = 48;        // dataflow placement: cost units between a producer's finish and its consumer
+  bool tc = false;       // mode 0: the leaf outputs on the tensor-core leaf kernel
   size_t smem = 0;
   double tuned_ms = 0;   // the chosen candidate's time (0: not tuned)
   int candidates = 0;    // candidates the autotuner timed
@@ -932,7 +910,7 @@ struct ChainSet {
 struct FlowPlan {
   std::vector<std::vector<std::vector<WItem>>> terms;   // [depth][group chain] -> uncut terms
   long long xh_tiles = 0;                               // row tiles the plan writes in xh
-  std::map<std::pair<int, int>, ChainSet> sets;         // (MT, item bytes) -> chains
+  std::map<std::tuple<int, int, int>, ChainSet> sets;   // (MT, item bytes, tc) -> chains
   LaunchShape shape[3];
 };
 
@@ -969,6 +947,7 @@ void flow_plan_build(const std::vector<NatTask>& lt, void** plan_out) {
           w.ntl = (unsigned char)ntl;
           w.x_buf = (unsigned char)tm.x_buf;
           w.y_buf = (unsigned char)L.y_buf;
+          w.flags = L.tc_out ? 4 : 0;   // kept only in the chains of the tensor-core leaf shape
           ch.push_back(w);
         }
         if (ch.empty()) {   // every input is empty: the group is zero
@@ -976,6 +955,7 @@ void flow_plan_build(const std::vector<NatTask>& lt, void** plan_out) {
           w.y_tile = L.y_tile + (long long)g * L.ng;
           w.ntl = (unsigned char)ntl;
           w.y_buf = (unsigned char)L.y_buf;
+          w.flags = L.tc_out ? 4 : 0;
           ch.push_back(w);
         }
         P->terms[(size_t)L.depth].push_back(std::move(ch));
@@ -994,12 +974,15 @@ void flow_plan_build(const std::vector<NatTask>& lt, void** plan_out) {
 // The chains of one term chain cut for (MT, item bytes): each term's
 // k-steps in runs of at most item_ks; the first item zeroes the
 // accumulators, the last stores them.
-static void cut_chain(const std::vector<WItem>& tc, int MT, int item_bytes, std::vector<WItem>& out,
+static void cut_chain(const std::vector<WItem>& tc, int MT, int item_bytes, bool tc_layout, std::vector<WItem>& out,
                       int& stage_bytes) {
   const size_t first = out.size();
+  const unsigned char keep = tc_layout ? 4 : 0;   // outputs in the tensor-core operand layout
   for (const WItem& t : tc) {
     if (t.ks == 0) {
-      out.push_back(t);
+      WItem w = t;
+      w.flags = t.flags & keep;
+      out.push_back(w);
       continue;
     }
     const int kc = item_ks(t.ntl, MT, item_bytes);
@@ -1008,7 +991,7 @@ static void cut_chain(const std::vector<WItem>& tc, int MT, int item_bytes, std:
       w.f_tile = t.f_tile + (long long)k0 * t.ntl;
       w.x_tile = t.x_tile + k0;
       w.ks = (short)std::min(kc, (int)t.ks - k0);
-      w.flags = 0;
+      w.flags = t.flags & keep;
       out.push_back(w);
       stage_bytes = std::max(stage_bytes, (int)t.ntl * (int)w.ks * 512 + (int)w.ks * MT * 1024);
     }
@@ -1017,16 +1000,20 @@ static void cut_chain(const std::vector<WItem>& tc, int MT, int item_bytes, std:
   out.back().flags |= 2;
 }
 
-static ChainSet& chain_set(FlowPlan* P, int MT, int item_bytes) {
-  auto key = std::make_pair(MT, item_bytes);
+// The chains for one shape; with tc the last depth (the leaf outputs) is
+// left to the tensor-core leaf kernel and the chains feeding it store their
+// outputs in its operand layout.
+static ChainSet& chain_set(FlowPlan* P, int MT, int item_bytes, bool tc) {
+  auto key = std::make_tuple(MT, item_bytes, tc ? 1 : 0);
   auto it = P->sets.find(key);
   if (it != P->sets.end()) return it->second;
   ChainSet cs;
-  cs.by_depth.assign(P->terms.size(), {});
-  for (size_t d = 0; d < P->terms.size(); ++d)
-    for (const auto& tc : P->terms[d]) {
+  const size_t nd = P->terms.size() - (tc ? 1 : 0);
+  cs.by_depth.assign(nd, {});
+  for (size_t d = 0; d < nd; ++d)
+    for (const auto& tch : P->terms[d]) {
       std::vector<WItem> ch;
-      cut_chain(tc, MT, item_bytes, ch, cs.stage_bytes);
+      cut_chain(tch, MT, item_bytes, tc, ch, cs.stage_bytes);
       cs.by_depth[d].push_back(std::move(ch));
     }
   return P->sets.emplace(key, std::move(cs)).first->second;
@@ -1219,12 +1206,14 @@ static void build_flow_streams(ChainSet& cs, int grid, int slack, long long xh_t
 }
 
 template <int MT>
-static void set_shape(FlowPlan* P, LaunchShape& L, int mode, int item_bytes, int pub, int slack) {
+static void set_shape(FlowPlan* P, LaunchShape& L, int mode, int item_bytes, int pub, int slack, bool tc) {
   int dev = 0, nsm = 0, optin = 0;
   HB_CUDA(cudaGetDevice(&dev));
   HB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   HB_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  ChainSet& cs = chain_set(P, MT, item_bytes);
+  if (tc && mode != 0) throw Error{HB_ERR_UNSUPPORTED, "the tensor-core leaf kernel runs with one launch per depth"};
+  ChainSet& cs = chain_set(P, MT, item_bytes, tc);
+  L.tc = tc;
   cudaFuncAttributes fa{};
   const void* k = mode == 0 ? (const void*)bf_step_kernel<MT> : (const void*)bf_flow_kernel<MT>;
   HB_CUDA(cudaFuncGetAttributes(&fa, k));
@@ -1251,6 +1240,9 @@ struct LaunchCtx {
   const double2* s;
   double scale;
   uint4* x;
+  uint4* x_tc;
+  void* tc_plan;
+  const void* F_tc;
   uint4* xh;
   double2* u;
   const long long* pperm;
@@ -1267,9 +1259,9 @@ struct LaunchCtx {
 template <int MT>
 static void launch_shape(FlowPlan* P, const LaunchShape& L, const LaunchCtx& c,
                          const std::function<void(int, bool)>& timer) {
-  ChainSet& cs = chain_set(P, MT, L.item_bytes);
+  ChainSet& cs = chain_set(P, MT, L.item_bytes, L.tc);
   if (L.mode == 0) {
-    gather_native(c.s, c.pperm, c.x, c.nv_tiles, c.Nv, c.R, MT, c.scale, c.st);
+    gather_native(c.s, c.pperm, c.x, L.tc ? c.x_tc : nullptr, c.nv_tiles, c.Nv, c.R, MT, c.scale, c.st);
     if (cs.depth_grid != L.grid) build_depth_streams(cs, L.grid);
     bool first = true;   // the timer brackets all depth launches (PDL stays intact)
     for (const DepthStreams& ds : cs.depth_streams) {
@@ -1289,6 +1281,11 @@ static void launch_shape(FlowPlan* P, const LaunchShape& L, const LaunchCtx& c,
       if (first) timer(0, true);
       first = false;
       HB_CUDA(cudaLaunchKernelEx(&cfg, bf_step_kernel<MT>, args));
+    }
+    if (L.tc) {   // the leaf outputs (the last depth) on the tensor cores
+      if (first) timer(0, true);
+      first = false;
+      tc_leaf_launch(c.tc_plan, MT, c.F_tc, c.x_tc, c.xh, c.u, c.pperm, c.Nv, c.R, c.err, c.budget, c.st);
     }
     if (!first) timer(0, false);
     return;
@@ -1331,11 +1328,11 @@ static void launch_shape(FlowPlan* P, const LaunchShape& L, const LaunchCtx& c,
 template <int MT>
 static void autotune(FlowPlan* P, LaunchShape& L, const LaunchCtx& c) {
   struct Cand {
-    int mode, item_bytes, pub, slack;
+    int mode, item_bytes, pub, slack, tc;
   };
-  const Cand cands[] = {{0, 16384, 1, 0},  {0, 8192, 1, 0},   {1, 16384, 1, 16}, {1, 16384, 1, 48},
-                        {1, 16384, 1, 128}, {1, 16384, 4, 48}, {1, 8192, 1, 16},  {1, 8192, 1, 48},
-                        {1, 8192, 1, 128}};
+  const Cand cands[] = {{0, 16384, 1, 0, 0},  {0, 8192, 1, 0, 0},   {0, 16384, 1, 0, 1},  {0, 8192, 1, 0, 1},
+                        {1, 16384, 1, 16, 0}, {1, 16384, 1, 48, 0}, {1, 16384, 1, 128, 0}, {1, 16384, 4, 48, 0},
+                        {1, 8192, 1, 16, 0},  {1, 8192, 1, 48, 0},  {1, 8192, 1, 128, 0}};
   cudaEvent_t e0, e1;
   HB_CUDA(cudaEventCreate(&e0));
   HB_CUDA(cudaEventCreate(&e1));
@@ -1347,7 +1344,7 @@ static void autotune(FlowPlan* P, LaunchShape& L, const LaunchCtx& c) {
     for (const Cand& k : cands) {
       LaunchShape T;
       try {
-        set_shape<MT>(P, T, k.mode, k.item_bytes, k.pub, k.slack);
+        set_shape<MT>(P, T, k.mode, k.item_bytes, k.pub, k.slack, k.tc != 0);
       } catch (const Error&) {
         continue;   // does not fit: not a candidate
       }
@@ -1381,14 +1378,15 @@ static void autotune(FlowPlan* P, LaunchShape& L, const LaunchCtx& c) {
   L = win;
   // keep only the winner's chains and streams
   for (auto it = P->sets.begin(); it != P->sets.end();) {
-    if (it->first.first == MT && it->first.second != L.item_bytes) {
+    if (std::get<0>(it->first) == MT &&
+        (std::get<1>(it->first) != L.item_bytes || std::get<2>(it->first) != (L.tc ? 1 : 0))) {
       free_set(it->second);
       it = P->sets.erase(it);
     } else {
       ++it;
     }
   }
-  ChainSet& cs = chain_set(P, MT, L.item_bytes);
+  ChainSet& cs = chain_set(P, MT, L.item_bytes, L.tc);
   for (auto it = cs.flow_streams.begin(); it != cs.flow_streams.end();) {
     if (L.mode == 0 || it->first != L.slack) {
       free_streams(it->second);
@@ -1411,20 +1409,22 @@ static void run_mt(FlowPlan* P, const LaunchCtx& c, int tune, const std::functio
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     HB_CUDA(cudaStreamIsCapturing(c.st, &cap));
     if (tune == 1 && cap == cudaStreamCaptureStatusNone) autotune<MT>(P, L, c);
-    else if (tune == 2) set_shape<MT>(P, L, 1, ITEM_BYTES, 1, 48);
-    else set_shape<MT>(P, L, 0, ITEM_BYTES, 1, 0);
+    else if (tune == 2) set_shape<MT>(P, L, 1, ITEM_BYTES, 1, 48, false);
+    else if (tune == 3) set_shape<MT>(P, L, 0, ITEM_BYTES, 1, 0, true);
+    else set_shape<MT>(P, L, 0, ITEM_BYTES, 1, 0, false);
   }
   launch_shape<MT>(P, L, c, timer);
 }
 
-void flow_launch(void* plan, const uint4* F, const double2* s, double scale, uint4* x, uint4* xh, double2* u,
-                 const long long* pperm, long long Nv, long long nv_tiles, int R, unsigned* flags, unsigned* epoch,
-                 int* err, long long budget_cycles, bool selftest, int autotune_on, cudaStream_t st,
-                 const std::function<void(int, bool)>& timer) {
+void flow_launch(void* plan, void* tc_plan, const void* F_tc, const uint4* F, const double2* s, double scale,
+                 uint4* x, uint4* x_tc, uint4* xh, double2* u, const long long* pperm, long long Nv,
+                 long long nv_tiles, int R, unsigned* flags, unsigned* epoch, int* err, long long budget_cycles,
+                 bool selftest, int autotune_on, cudaStream_t st, const std::function<void(int, bool)>& timer) {
   FlowPlan* P = static_cast<FlowPlan*>(plan);
   if (P->terms.empty()) return;
   const int MT = (R + 15) / 16;
-  const LaunchCtx c{F, s, scale, x, xh, u, pperm, Nv, nv_tiles, R, flags, epoch, err, budget_cycles, selftest, st};
+  const LaunchCtx c{F,     s,      scale, x,    x_tc,          tc_plan,  F_tc, xh, u, pperm, Nv, nv_tiles, R,
+                    flags, epoch, err,   budget_cycles, selftest, st};
   if (MT == 1) run_mt<1>(P, c, autotune_on, timer);
   else if (MT == 2) run_mt<2>(P, c, autotune_on, timer);
   else throw Error{HB_ERR_UNSUPPORTED, "the mixed apply takes 1 or 2 m-tiles of 16 right-hand sides per pass"};
@@ -1434,7 +1434,7 @@ void flow_shape(const void* plan, int MT, int* mode, int* item_bytes, int* stage
                 double* tuned_ms, int* candidates) {
   const FlowPlan* P = static_cast<const FlowPlan*>(plan);
   const LaunchShape& L = P->shape[MT];
-  *mode = L.ready ? L.mode : -1;
+  *mode = L.ready ? (L.mode == 0 && L.tc ? 2 : L.mode) : -1;
   *item_bytes = L.item_bytes;
   *stages = L.stages;
   *pub = L.pub;

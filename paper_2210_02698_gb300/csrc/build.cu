@@ -24,6 +24,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <map>
 #include <cmath>
 #include <vector>
 
@@ -594,6 +595,7 @@ static void make_plans(hb_ctx* c, std::vector<Butterfly>& bfs, const std::vector
               for (int j = 0; j < w; ++j) {
                 const BlockRec& br = b.lev[k][(size_t)i * w + j];
                 NatTask t = task(br.xh_tile, tiles8(br.rank), k, 2);
+                t.tc_out = (k == b.L);   // lev[L] is read only by the leaf outputs (K^L)
                 if (k == 0) {
                   const long long leaf = ((long long)b.si << b.L) + j;
                   const int nn = leaf_size(leaf);
@@ -636,6 +638,7 @@ static void make_plans(hb_ctx* c, std::vector<Butterfly>& bfs, const std::vector
             const long long leaf = ((long long)b.oi << b.L) + i;
             const int sz = leaf_size(leaf);
             NatTask t = task(br.xh_tile, tiles8(br.rank), 0, 2);
+            t.tc_out = (b.L == 0);   // lev[0] is read only by the leaf outputs (V^0^H)
             t.terms.push_back(term(nat(b.kl_off[(size_t)i], sz, br.rank, 0, sz, 0), c->leaf_tile[(size_t)leaf],
                                    tiles8(sz), 0));
             nt.push_back(std::move(t));
@@ -654,6 +657,7 @@ static void make_plans(hb_ctx* c, std::vector<Butterfly>& bfs, const std::vector
                 const BlockRec& o1 = b.lev[tl - 1][q1];
                 const BlockRec& o2 = b.lev[tl - 1][q1 + 1];
                 NatTask t = task(o1.xh_tile, tiles8(o1.rank) + tiles8(o2.rank), d, 2);
+                t.tc_out = (tl == 1);   // writes lev[0], read only by the leaf outputs
                 for (int cc = 0; cc < 2; ++cc) {
                   const BlockRec& br = b.lev[tl][(size_t)(2 * p + cc) * w + j];
                   t.terms.push_back(term(nat(br.f_off, br.rank, o1.rank, o2.rank, br.rank, 0), br.xh_tile,
@@ -682,6 +686,43 @@ static void make_plans(hb_ctx* c, std::vector<Butterfly>& bfs, const std::vector
       c->d_nat[dir] = dev_alloc<uint4>((size_t)std::max<long long>(ntile, 1) * 32);
       nat_convert(c->d_f64, nb, c->d_nat[dir], st);
       HB_CUDA(cudaStreamSynchronize(st));
+      // the leaf outputs again, for the tensor-core leaf kernel: chains of up
+      // to 64 outputs, each term's block in the operand layout (4 KB per 8
+      // inputs); the terms and blocks are those of the native tasks above
+      {
+        std::vector<TcBlock> tb;
+        std::vector<TcChainHost> tch;
+        long long units = 0;
+        std::map<long long, const NatBlock*> by_tile;
+        for (const NatBlock& B : nb) by_tile[B.tile0] = &B;
+        for (const NatTask& L : nt) {
+          if (L.y_buf != 1) continue;
+          const int rows = 8 * L.nt;
+          for (int o0 = 0; o0 < rows; o0 += 64) {
+            TcChainHost ch;
+            ch.y_tile = L.y_tile + o0 / 8;
+            ch.nout = std::min(64, rows - o0);
+            for (const NatTerm& tm : L.terms) {
+              const NatBlock& B = *by_tile.at(tm.f_tile);
+              TcBlock t{};
+              t.src_off = B.src_off;
+              t.unit0 = units;
+              t.ld = B.ld;
+              t.conj = B.conj;
+              t.o0 = o0;
+              t.nout = std::max(0, std::min(64, B.r1 - o0));
+              t.k = B.k1;
+              tb.push_back(t);
+              ch.terms.push_back(TcTerm{units, tm.x_tile, tm.ks, tm.x_buf});
+              units += tm.ks;
+            }
+            tch.push_back(std::move(ch));
+          }
+        }
+        c->d_tc[dir] = dev_alloc<uint4>((size_t)std::max<long long>(units, 1) * 256);
+        tc_convert(c->d_f64, tb, c->d_tc[dir], st);
+        c->tc_plan[dir] = tc_plan_build(std::move(tch));
+      }
       flow_plan_build(nt, &c->flow_plan[dir]);
     }
   }

@@ -148,14 +148,43 @@ struct NatTerm {
   int x_buf;
 };
 // A task writes nt row tiles of buffer y_buf from y_tile on as the sum of
-// its terms; depth d reads only what depths < d wrote.
+// its terms; depth d reads only what depths < d wrote.  tc_out: only the
+// leaf outputs read what it writes (the tensor-core leaf kernel can take
+// it in its operand layout).
 struct NatTask {
   long long y_tile;
   int nt;
   int depth;
   int y_buf;
   int ng;                // n-tiles per group of its blocks
+  bool tc_out = false;
   std::vector<NatTerm> terms;
+};
+
+// Tensor-core leaf outputs (leaf_tc.cu).  TcBlock: outputs o0 .. o0 + nout
+// (<= 64) of op(F) (as NatBlock: column-major FP64 block at src_off, leading
+// dimension ld, conjugate transpose when conj) with k inputs, converted to
+// ceil(k / 8) 4 KB units from unit0 of the tc arena.  TcTerm: nkg units
+// from unit0 times the input row tiles x_tile .. (x_buf 0 = the operand-layout
+// copy of x, 2 = xh).  TcChainHost: one chain of up to 64 outputs from padded
+// row tile y_tile on, written to u in natural order.
+struct TcBlock {
+  long long src_off;
+  long long unit0;
+  int ld, conj;
+  int o0, nout, k;
+  int pad;
+};
+struct TcTerm {
+  long long unit0;
+  long long x_tile;
+  int nkg;
+  int x_buf;
+};
+struct TcChainHost {
+  long long y_tile;
+  int nout;
+  std::vector<TcTerm> terms;
 };
 
 // Factor index of one butterfly (what hb_save writes besides the arena):
@@ -228,6 +257,9 @@ struct hb_ctx {
   double2* d_f64 = nullptr;
   // native split-BF16 arenas of the mixed apply: [0] forward, [1] adjoint (512-byte tiles)
   uint4* d_nat[2] = {nullptr, nullptr};
+  // operand-layout arenas of the tensor-core leaf outputs (4 KB units) and their plans
+  uint4* d_tc[2] = {nullptr, nullptr};
+  void* tc_plan[2] = {nullptr, nullptr};
   long long nat_tiles[2] = {0, 0};
   std::vector<long long> leaf_tile;   // first padded row tile of every leaf (+ total)
   long long nv_tiles = 0;             // row tiles of the padded tree-ordered vectors
@@ -251,6 +283,7 @@ struct hb_ctx {
   void* d_xh = nullptr;
   // mixed apply scratch (native layout, up to 32 right-hand sides)
   uint4* d_mx = nullptr;
+  uint4* d_mx_tc = nullptr;   // x again in the tensor-core operand layout
   uint4* d_mxh = nullptr;
   // readiness flags of the dataflow launch (x row tiles, then xh row tiles)
   // and its launch counter ([0] launches completed, [1] CTAs done)
@@ -311,15 +344,20 @@ int flow_plan_depths(const void* plan);
 // R <= 32 right-hand sides: gather of s (scaled), every depth, the last
 // depth writing u (natural order) itself; one launch per depth or one
 // persistent dataflow launch (flags / epoch: its readiness words)
-void flow_launch(void* plan, const uint4* F, const double2* s, double scale, uint4* x, uint4* xh, double2* u,
-                 const long long* pperm, long long Nv, long long nv_tiles, int R, unsigned* flags, unsigned* epoch,
-                 int* err, long long budget_cycles, bool selftest, int autotune_on, cudaStream_t st,
-                 const std::function<void(int, bool)>& timer);
+void flow_launch(void* plan, void* tc_plan, const void* F_tc, const uint4* F, const double2* s, double scale,
+                 uint4* x, uint4* x_tc, uint4* xh, double2* u, const long long* pperm, long long Nv,
+                 long long nv_tiles, int R, unsigned* flags, unsigned* epoch, int* err, long long budget_cycles,
+                 bool selftest, int autotune_on, cudaStream_t st, const std::function<void(int, bool)>& timer);
 void flow_shape(const void* plan, int MT, int* mode, int* item_bytes, int* stages, int* pub, int* slack,
                 double* tuned_ms, int* candidates);
 void nat_convert(const double2* F64, const std::vector<NatBlock>& blocks, uint4* out, cudaStream_t st);
-void gather_native(const double2* s, const long long* pperm, uint4* x, long long nv_tiles, long long Nv, int R,
-                   int MT, double scale, cudaStream_t st);
+void tc_convert(const double2* F64, const std::vector<TcBlock>& blocks, void* out, cudaStream_t st);
+void* tc_plan_build(std::vector<TcChainHost>&& chains);
+void tc_plan_free(void* plan);
+void tc_leaf_launch(void* plan, int MT, const void* F, const uint4* x, const uint4* xh, double2* u,
+                    const long long* pperm, long long Nv, int R, int* err, long long budget, cudaStream_t st);
+void gather_native(const double2* s, const long long* pperm, uint4* x, uint4* x_tc, long long nv_tiles, long long Nv,
+                   int R, int MT, double scale, cudaStream_t st);
 void apply_bf(hb_ctx* c, const double2* s, double2* u, int nrhs, int adjoint, int precision,
               cudaStream_t st);
 // inclusion.cu
