@@ -190,6 +190,31 @@ hb_status hb_apply_adjoint(hb_handle h, const void* u, void* s, int nrhs, void* 
 hb_status hb_save(hb_handle h, const char* path);
 hb_status hb_load(const char* path, hb_handle* out);
 
+/* Shards of the apply for several devices (Sec. 4.2: each off-diagonal
+ * butterfly K(o, s) of the HODBF writes only the rows of o, so the rows
+ * split by cluster-tree subtree).  Rank `rank` of `nranks` (a power of two,
+ * at most 2^L_v) owns node `rank` of level log2(nranks) of the cluster tree:
+ * the tree positions [*lo, *hi) (hb_shard_rows; their natural indices are
+ * hb_tree_perm's entries lo .. hi - 1).
+ * hb_apply_shard: s is the whole input (every rank's cells, natural order,
+ * as after an all-gather); computes every task whose rows meet the rank's
+ * and writes u on the rank's cells only (other cells of u untouched).  Its
+ * values there equal hb_apply's bit for bit.
+ * hb_apply_shard_adjoint: u holds the rank's cells (its other cells are
+ * ignored, read as zero); computes the tasks whose rows meet the rank's
+ * with the other ranks' skeleton vectors zero and writes the rank's share
+ * of s = h^2 K^H u on every cell; the shares of all ranks add up to
+ * hb_apply_adjoint's result (a reduce-scatter or all-reduce across ranks).
+ * Both run with the handle's precision, one launch per dependency depth in
+ * the mixed path.  Errors as hb_apply; HB_ERR_ARG for a bad nranks / rank. */
+hb_status hb_shard_rows(hb_handle h, int nranks, int rank, long long* lo, long long* hi);
+hb_status hb_apply_shard(hb_handle h, const void* s, void* u, int nrhs, int nranks, int rank, void* stream);
+hb_status hb_apply_shard_adjoint(hb_handle h, const void* u, void* s, int nrhs, int nranks, int rank,
+                                 void* stream);
+/* hb_host_shard_rows: hb_shard_rows for an nx x ny grid and leaf size,
+ * without a handle or a device. */
+hb_status hb_host_shard_rows(int nx, int ny, int leaf, int nranks, int rank, long long* lo, long long* hi);
+
 /* hb_set_precision: HB_FP64 or HB_MIXED_BF16X3 for later applies. */
 hb_status hb_set_precision(hb_handle h, int precision);
 

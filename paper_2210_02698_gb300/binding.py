@@ -26,6 +26,7 @@ EXPORTS = ["hb_create", "hb_build", "hb_save", "hb_load", "hb_apply", "hb_apply_
            "hb_apply_dense", "hb_apply_dense_adjoint", "hb_entries", "hb_curve_set", "hb_curve_operators",
            "hb_apply_inclusion", "hb_id_batch", "hb_id_batch_noalloc",
            "hb_record_id_blocks", "hb_recorded_id_count", "hb_recorded_id_block", "hb_launch_shape", "hb_fp64_fma_peak",
+           "hb_shard_rows", "hb_apply_shard", "hb_apply_shard_adjoint", "hb_host_shard_rows",
            "hb_tree_perm", "hb_proxy_rows", "hb_host_cluster_tree", "hb_host_proxy_rows", "hb_host_segment_tree", "hb_host_point_proxy_rows", "hb_info", "hb_rank_profile", "hb_set_kernel_timing",
            "hb_kernel_times", "hb_last_error", "hb_destroy"]
 
@@ -84,6 +85,10 @@ def lib():
         L.hb_launch_shape.argtypes = [vp, i, i, C.POINTER(i), C.POINTER(i), C.POINTER(i), C.POINTER(i),
                                       C.POINTER(i), C.POINTER(d), C.POINTER(i)]
         L.hb_fp64_fma_peak.argtypes = [C.POINTER(d), vp]
+        L.hb_shard_rows.argtypes = [vp, i, i, C.POINTER(ll), C.POINTER(ll)]
+        L.hb_apply_shard.argtypes = [vp, vp, vp, i, i, i, vp]
+        L.hb_apply_shard_adjoint.argtypes = [vp, vp, vp, i, i, i, vp]
+        L.hb_host_shard_rows.argtypes = [i, i, i, i, i, C.POINTER(ll), C.POINTER(ll)]
         L.hb_record_id_blocks.argtypes = [vp, i]
         L.hb_recorded_id_count.argtypes = [vp, C.POINTER(i)]
         L.hb_recorded_id_block.argtypes = [vp, i, C.POINTER(i), C.POINTER(i), C.POINTER(i), vp, vp, vp,
@@ -225,6 +230,22 @@ class Operator:
 
     def apply_adjoint(self, u, s, nrhs, stream=None):
         self._call("hb_apply_adjoint", *self._vecs(u, s, nrhs), int(nrhs), _stream_ptr(stream))
+
+    def shard_rows(self, nranks, rank):
+        """hb_shard_rows: the tree positions [lo, hi) of rank `rank` of `nranks`."""
+        lo, hi = C.c_longlong(), C.c_longlong()
+        self._call("hb_shard_rows", int(nranks), int(rank), C.byref(lo), C.byref(hi))
+        return lo.value, hi.value
+
+    def apply_shard(self, s, u, nrhs, nranks, rank, stream=None):
+        """hb_apply_shard: this rank's rows of u from the whole input s."""
+        self._call("hb_apply_shard", *self._vecs(s, u, nrhs), int(nrhs), int(nranks), int(rank),
+                   _stream_ptr(stream))
+
+    def apply_shard_adjoint(self, u, s, nrhs, nranks, rank, stream=None):
+        """hb_apply_shard_adjoint: this rank's share of the adjoint on every cell."""
+        self._call("hb_apply_shard_adjoint", *self._vecs(u, s, nrhs), int(nrhs), int(nranks), int(rank),
+                   _stream_ptr(stream))
 
     def apply_dense(self, s, u, nrhs, stream=None):
         self._call("hb_apply_dense", *self._vecs(s, u, nrhs), int(nrhs), _stream_ptr(stream))
@@ -427,6 +448,14 @@ def fp64_fma_peak(stream=None):
     v = C.c_double()
     _check(lib().hb_fp64_fma_peak(C.byref(v), _stream_ptr(stream)))
     return v.value
+
+
+def host_shard_rows(nx, ny, leaf, nranks, rank):
+    """hb_host_shard_rows: a rank's tree positions [lo, hi) without a device."""
+    lo, hi = C.c_longlong(), C.c_longlong()
+    _check(lib().hb_host_shard_rows(int(nx), int(ny), int(leaf), int(nranks), int(rank), C.byref(lo),
+                                    C.byref(hi)))
+    return lo.value, hi.value
 
 
 def load_tables(path):

@@ -122,6 +122,7 @@ void free_all(hb_ctx* c) {
   hb::flow_plan_free(c->flow_plan[1]);
   hb::tc_plan_free(c->tc_plan[0]);
   hb::tc_plan_free(c->tc_plan[1]);
+  hb::shard_cache_free(c);
   hb::curve_free(c);
   if (c->h_err) cudaFreeHost(c->h_err);
 }
@@ -331,6 +332,31 @@ hb_status hb_apply_adjoint(hb_handle h, const void* u, void* s, int nrhs, void* 
   });
 }
 
+hb_status hb_shard_rows(hb_handle h, int nranks, int rank, long long* lo, long long* hi) {
+  return guarded(h, [&] {
+    if (!h || !lo || !hi) throw hb::arg_error("null argument");
+    hb::shard_rows(h, nranks, rank, lo, hi);
+  });
+}
+
+hb_status hb_apply_shard(hb_handle h, const void* s, void* u, int nrhs, int nranks, int rank, void* stream) {
+  return guarded(h, [&] {
+    check_vec_args(h, s, u, nrhs);
+    if (!h->built) throw hb::Error{HB_ERR_STATE, "hb_apply_shard before hb_build"};
+    hb::apply_bf_shard(h, (const double2*)s, (double2*)u, nrhs, 0, h->opt.precision, nranks, rank,
+                       (cudaStream_t)stream);
+  });
+}
+
+hb_status hb_apply_shard_adjoint(hb_handle h, const void* u, void* s, int nrhs, int nranks, int rank, void* stream) {
+  return guarded(h, [&] {
+    check_vec_args(h, u, s, nrhs);
+    if (!h->built) throw hb::Error{HB_ERR_STATE, "hb_apply_shard_adjoint before hb_build"};
+    hb::apply_bf_shard(h, (const double2*)u, (double2*)s, nrhs, 1, h->opt.precision, nranks, rank,
+                       (cudaStream_t)stream);
+  });
+}
+
 hb_status hb_set_precision(hb_handle h, int precision) {
   return guarded(h, [&] {
     if (!h) throw hb::arg_error("null handle");
@@ -494,6 +520,15 @@ void host_tree_ctx(hb_ctx& c, int nx, int ny, int leaf) {
   hb::tree_build(&c);
 }
 }  // namespace
+
+hb_status hb_host_shard_rows(int nx, int ny, int leaf, int nranks, int rank, long long* lo, long long* hi) {
+  return guarded(nullptr, [&] {
+    if (!lo || !hi) throw hb::arg_error("null argument");
+    hb_ctx c;
+    host_tree_ctx(c, nx, ny, leaf);
+    hb::shard_rows(&c, nranks, rank, lo, hi);
+  });
+}
 
 hb_status hb_host_cluster_tree(int nx, int ny, int leaf, long long* perm_out, long long* bounds_out, int* levels) {
   return guarded(nullptr, [&] {

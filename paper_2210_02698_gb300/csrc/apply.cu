@@ -13,6 +13,7 @@
 
 #include <algorithm>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "hb_internal.cuh"
@@ -45,28 +46,30 @@ struct Real<float2> {
 };
 
 // x[p][r] = scale * s[r*Nv + perm[p]]   (column-major natural -> row-major tree order)
+// for tree positions p in [lo, hi); 0 elsewhere (a shard's share of the input)
 template <class C>
 __global__ void gather_kernel(const double2* __restrict__ s, const long long* __restrict__ perm, C* __restrict__ x,
-                              long long Nv, int R, double scale) {
+                              long long Nv, int R, double scale, long long lo, long long hi) {
   long long total = Nv * R;
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
     long long p = idx / R;
     int r = (int)(idx % R);
-    double2 v = s[(size_t)r * Nv + perm[p]];
+    const double2 v = (p >= lo && p < hi) ? s[(size_t)r * Nv + perm[p]] : make_double2(0.0, 0.0);
     x[idx] = Real<C>::make((typename Real<C>::T)(v.x * scale), (typename Real<C>::T)(v.y * scale));
   }
 }
 
+// u[r*Nv + perm[p]] = y[p][r] for tree positions p in [lo, hi)
 template <class C>
 __global__ void scatter_kernel(const C* __restrict__ y, const long long* __restrict__ perm, double2* __restrict__ u,
-                               long long Nv, int R) {
-  long long total = Nv * R;
+                               long long Nv, int R, long long lo, long long hi) {
+  long long total = (hi - lo) * R;
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
-    long long p = idx / R;
+    long long p = lo + idx / R;
     int r = (int)(idx % R);
-    C v = y[idx];
+    C v = y[(size_t)p * R + r];
     u[(size_t)r * Nv + perm[p]] = make_double2((double)v.x, (double)v.y);
   }
 }
@@ -239,12 +242,12 @@ void apply_bf(hb_ctx* c, const double2* s, double2* u, int nrhs, int adjoint, in
     const int grid = (int)std::min<long long>((total + 255) / 256, 152LL * 16);
     if (precision == HB_FP64) {
       ts.begin("gather");
-      gather_kernel<double2><<<grid, 256, 0, st>>>(sc, c->d_perm, (double2*)c->d_x, c->Nv, R, scale);
+      gather_kernel<double2><<<grid, 256, 0, st>>>(sc, c->d_perm, (double2*)c->d_x, c->Nv, R, scale, 0, c->Nv);
       HB_CHECK_LAUNCH();
       ts.end();
       run_steps<double2>(c, c->d_f64, R, adjoint, st, ts);
       ts.begin("scatter");
-      scatter_kernel<double2><<<grid, 256, 0, st>>>((double2*)c->d_y, c->d_perm, uc, c->Nv, R);
+      scatter_kernel<double2><<<grid, 256, 0, st>>>((double2*)c->d_y, c->d_perm, uc, c->Nv, R, 0, c->Nv);
       HB_CHECK_LAUNCH();
       ts.end();
     } else {
@@ -262,6 +265,125 @@ void apply_bf(hb_ctx* c, const double2* s, double2* u, int nrhs, int adjoint, in
     }
   }
   ts.finish();
+}
+
+// ------------------------------------------------------------- shards ----
+// Rank `rank` of `nranks` (a power of two, at most 2^L_v) owns node `rank`
+// of level log2(nranks) of the cluster tree: the tree positions [lo, hi).
+void shard_rows(const hb_ctx* c, int nranks, int rank, long long* lo, long long* hi) {
+  if (nranks < 1 || (nranks & (nranks - 1)) || rank < 0 || rank >= nranks)
+    throw arg_error("nranks must be a power of two and 0 <= rank < nranks (got %d, %d)", nranks, rank);
+  int k = 0;
+  while ((1 << k) < nranks) ++k;
+  if (k > c->Lv) throw arg_error("nranks=%d exceeds the %lld leaves of the cluster tree", nranks, 1LL << c->Lv);
+  *lo = c->bounds[k][rank];
+  *hi = c->bounds[k][rank + 1];
+}
+
+namespace {
+struct ShardSteps {
+  std::vector<int> begin;
+  Task* d_tasks = nullptr;
+};
+}  // namespace
+
+// The FP64 step lists of one shard: the tasks whose rows meet [lo, hi).
+static ShardSteps& shard_steps(hb_ctx* c, int dir, long long lo, long long hi) {
+  static_assert(sizeof(void*) == 8, "");
+  auto key = std::make_tuple(dir, lo, hi);
+  auto it = c->shard_cache.find(key);
+  if (it != c->shard_cache.end()) return *static_cast<ShardSteps*>(it->second);
+  ShardSteps* S = new ShardSteps();
+  std::vector<Task> keep;
+  const std::vector<int>& sb = c->step_begin[dir];
+  for (size_t q = 0; q + 1 < sb.size(); ++q) {
+    S->begin.push_back((int)keep.size());
+    for (int t = sb[q]; t < sb[q + 1]; ++t) {
+      const auto& rr = c->task_rows[dir][(size_t)t];
+      if (rr.first < hi && rr.second > lo) keep.push_back(c->tasks_h[dir][(size_t)t]);
+    }
+  }
+  S->begin.push_back((int)keep.size());
+  try {
+    S->d_tasks = upload(keep);
+  } catch (...) {
+    delete S;
+    throw;
+  }
+  c->shard_cache[key] = S;
+  return *S;
+}
+
+void shard_cache_free(hb_ctx* c) {
+  for (auto& kv : c->shard_cache) {
+    ShardSteps* S = static_cast<ShardSteps*>(kv.second);
+    dev_free(S->d_tasks);
+    delete S;
+  }
+  c->shard_cache.clear();
+}
+
+// The padded row (mixed path) where the leaf starting at tree position pos
+// starts (pos = N_v: the end).
+static long long padded_row_of(const hb_ctx* c, long long pos) {
+  const std::vector<long long>& b = c->bounds[(size_t)c->Lv];
+  const auto it = std::lower_bound(b.begin(), b.end(), pos);
+  if (it == b.end() || *it != pos) throw Error{HB_ERR_STATE, "shard boundary is not a leaf boundary"};
+  return 8 * c->leaf_tile[(size_t)(it - b.begin())];
+}
+
+// One rank's share of the apply.  Forward (u = A s): s is the whole input
+// (natural order, every rank's cells); the rank computes every task whose
+// rows meet its own and writes u on its cells only.  Adjoint (s = A^H u):
+// u holds the rank's cells (the rest is ignored, read as zero); the rank
+// computes the tasks whose rows meet its own with the skeleton vectors of
+// the others zero, and writes its share of s on every cell; the shares of
+// all ranks add up to the adjoint.
+void apply_bf_shard(hb_ctx* c, const double2* s, double2* u, int nrhs, int adjoint, int precision, int nranks,
+                    int rank, cudaStream_t st) {
+  NvtxRange nr(adjoint ? "hb_apply_shard_adjoint" : "hb_apply_shard");
+  if (c->h_err && *reinterpret_cast<volatile int*>(c->h_err)) {
+    *reinterpret_cast<volatile int*>(c->h_err) = 0;
+    throw Error{HB_ERR_TIMEOUT, "a bounded device wait of an earlier apply gave up"};
+  }
+  long long lo = 0, hi = 0;
+  shard_rows(c, nranks, rank, &lo, &hi);
+  const int chunk = std::min(nrhs, precision == HB_FP64 ? 16 : 32);
+  ensure_scratch(c, chunk, precision == HB_FP64);
+  const double scale = c->h * c->h;
+  const long long glo = adjoint ? lo : 0, ghi = adjoint ? hi : c->Nv;    // input rows
+  const long long slo = adjoint ? 0 : lo, shi = adjoint ? c->Nv : hi;   // output rows
+  for (int r0 = 0; r0 < nrhs; r0 += chunk) {
+    const int R = std::min(chunk, nrhs - r0);
+    const double2* sc = s + (size_t)r0 * c->Nv;
+    double2* uc = u + (size_t)r0 * c->Nv;
+    const long long total = c->Nv * R;
+    const int grid = (int)std::min<long long>((total + 255) / 256, 152LL * 16);
+    if (precision == HB_FP64) {
+      gather_kernel<double2><<<grid, 256, 0, st>>>(sc, c->d_perm, (double2*)c->d_x, c->Nv, R, scale, glo, ghi);
+      HB_CHECK_LAUNCH();
+      if (adjoint) {
+        HB_CUDA(cudaMemsetAsync(c->d_y, 0, sizeof(double2) * (size_t)c->Nv * R, st));
+        HB_CUDA(cudaMemsetAsync(c->d_xh, 0, sizeof(double2) * (size_t)std::max<long long>(c->xh_rows, 1) * R, st));
+      }
+      ShardSteps& S = shard_steps(c, adjoint, lo, hi);
+      for (size_t q = 0; q + 1 < S.begin.size(); ++q) {
+        const int n = S.begin[q + 1] - S.begin[q];
+        if (n == 0) continue;
+        step_kernel<double2><<<n, 128, 0, st>>>(S.d_tasks + S.begin[q], c->d_f64, (double2*)c->d_x,
+                                               (double2*)c->d_y, (double2*)c->d_xh, R);
+        HB_CHECK_LAUNCH();
+      }
+      const int g2 = (int)std::max<long long>(1, std::min<long long>(((shi - slo) * R + 255) / 256, 152LL * 16));
+      scatter_kernel<double2><<<g2, 256, 0, st>>>((double2*)c->d_y, c->d_perm, uc, c->Nv, R, slo, shi);
+      HB_CHECK_LAUNCH();
+    } else {
+      flow_launch_shard(c->flow_plan[adjoint], c->d_nat[adjoint], sc, scale, c->d_mx, c->d_mxh, c->xh_tiles, uc,
+                        c->d_pperm, c->Nv, c->nv_tiles, R, lo, hi, adjoint ? padded_row_of(c, lo) : 0,
+                        adjoint ? padded_row_of(c, hi) : (long long)8 * c->nv_tiles, adjoint != 0, c->d_err,
+                        c->opt.barrier_cycles > 0 ? c->opt.barrier_cycles : (1LL << 31), st);
+    }
+  }
 }
 
 }  // namespace hb

@@ -813,7 +813,7 @@ __global__ void __launch_bounds__(256) gather_native_kernel(const double2* __res
                                                             const long long* __restrict__ pperm,
                                                             uint4* __restrict__ x, uint4* __restrict__ x_tc,
                                                             long long nv_tiles, long long Nv, int R, int MT,
-                                                            double scale) {
+                                                            double scale, long long win_lo, long long win_hi) {
   __shared__ __align__(16) uint32_t tile[8][256];
   __shared__ __align__(16) uint16_t ttc[8][512];
   // the first depth launch may start now and stream its factor runs; it
@@ -825,7 +825,8 @@ __global__ void __launch_bounds__(256) gather_native_kernel(const double2* __res
   const long long rt = wid / MT;
   const int mt = (int)(wid - rt * MT);
   const int r = lane & 7, c0 = 4 * (lane >> 3);
-  const long long nat = pperm[8 * rt + r];
+  const long long prow = 8 * rt + r;                    // padded row; outside [win_lo, win_hi) it reads as 0
+  const long long nat = (prow >= win_lo && prow < win_hi) ? pperm[prow] : -1;
   double2 v[4];
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
@@ -862,10 +863,11 @@ __global__ void __launch_bounds__(256) gather_native_kernel(const double2* __res
 }
 
 void gather_native(const double2* s, const long long* pperm, uint4* x, uint4* x_tc, long long nv_tiles, long long Nv,
-                   int R, int MT, double scale, cudaStream_t st) {
+                   int R, int MT, double scale, cudaStream_t st, long long win_lo, long long win_hi) {
   const long long warps = nv_tiles * MT;
   if (warps == 0) return;
-  gather_native_kernel<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(s, pperm, x, x_tc, nv_tiles, Nv, R, MT, scale);
+  gather_native_kernel<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(s, pperm, x, x_tc, nv_tiles, Nv, R, MT, scale,
+                                                                     win_lo, win_hi);
   HB_CHECK_LAUNCH();
 }
 
@@ -909,8 +911,9 @@ struct ChainSet {
 // items per (m-tile count, item size) on demand.
 struct FlowPlan {
   std::vector<std::vector<std::vector<WItem>>> terms;   // [depth][group chain] -> uncut terms
+  std::vector<std::vector<std::pair<long long, long long>>> rows;   // [depth][group chain] -> tree rows it serves
   long long xh_tiles = 0;                               // row tiles the plan writes in xh
-  std::map<std::tuple<int, int, int>, ChainSet> sets;   // (MT, item bytes, tc) -> chains
+  std::map<std::tuple<int, int, int, long long, long long>, ChainSet> sets;   // (MT, item bytes, tc, rows) -> chains
   LaunchShape shape[3];
 };
 
@@ -929,6 +932,7 @@ void flow_plan_build(const std::vector<NatTask>& lt, void** plan_out) {
     int maxd = -1;
     for (const NatTask& L : lt) maxd = std::max(maxd, L.depth);
     P->terms.assign((size_t)(maxd + 1), {});
+    P->rows.assign((size_t)(maxd + 1), {});
     for (const NatTask& L : lt) {
       if (L.nt <= 0) continue;
       if (L.ng < 1 || L.ng > NTW) throw Error{HB_ERR_UNSUPPORTED, "n-tile group larger than the accumulators"};
@@ -959,6 +963,7 @@ void flow_plan_build(const std::vector<NatTask>& lt, void** plan_out) {
           ch.push_back(w);
         }
         P->terms[(size_t)L.depth].push_back(std::move(ch));
+        P->rows[(size_t)L.depth].push_back({L.row_lo, L.row_hi});
       }
     }
     for (const NatTask& L : lt)
@@ -1003,15 +1008,18 @@ static void cut_chain(const std::vector<WItem>& tc, int MT, int item_bytes, bool
 // The chains for one shape; with tc the last depth (the leaf outputs) is
 // left to the tensor-core leaf kernel and the chains feeding it store their
 // outputs in its operand layout.
-static ChainSet& chain_set(FlowPlan* P, int MT, int item_bytes, bool tc) {
-  auto key = std::make_tuple(MT, item_bytes, tc ? 1 : 0);
+static ChainSet& chain_set(FlowPlan* P, int MT, int item_bytes, bool tc, long long lo = 0, long long hi = -1) {
+  auto key = std::make_tuple(MT, item_bytes, tc ? 1 : 0, lo, hi);
   auto it = P->sets.find(key);
   if (it != P->sets.end()) return it->second;
   ChainSet cs;
   const size_t nd = P->terms.size() - (tc ? 1 : 0);
   cs.by_depth.assign(nd, {});
   for (size_t d = 0; d < nd; ++d)
-    for (const auto& tch : P->terms[d]) {
+    for (size_t q = 0; q < P->terms[d].size(); ++q) {
+      const auto& tch = P->terms[d][q];
+      // a shard (hi >= 0) keeps the chains whose rows meet [lo, hi)
+      if (hi >= 0 && !(P->rows[d][q].first < hi && P->rows[d][q].second > lo)) continue;
       std::vector<WItem> ch;
       cut_chain(tch, MT, item_bytes, tc, ch, cs.stage_bytes);
       cs.by_depth[d].push_back(std::move(ch));
@@ -1378,7 +1386,7 @@ static void autotune(FlowPlan* P, LaunchShape& L, const LaunchCtx& c) {
   L = win;
   // keep only the winner's chains and streams
   for (auto it = P->sets.begin(); it != P->sets.end();) {
-    if (std::get<0>(it->first) == MT &&
+    if (std::get<0>(it->first) == MT && std::get<4>(it->first) < 0 &&
         (std::get<1>(it->first) != L.item_bytes || std::get<2>(it->first) != (L.tc ? 1 : 0))) {
       free_set(it->second);
       it = P->sets.erase(it);
@@ -1427,6 +1435,50 @@ void flow_launch(void* plan, void* tc_plan, const void* F_tc, const uint4* F, co
                     flags, epoch, err,   budget_cycles, selftest, st};
   if (MT == 1) run_mt<1>(P, c, autotune_on, timer);
   else if (MT == 2) run_mt<2>(P, c, autotune_on, timer);
+  else throw Error{HB_ERR_UNSUPPORTED, "the mixed apply takes 1 or 2 m-tiles of 16 right-hand sides per pass"};
+}
+
+template <int MT>
+static void launch_shard_mt(FlowPlan* P, const LaunchCtx& c, long long lo, long long hi, long long pad_lo,
+                            long long pad_hi, bool adjoint, long long xh_tiles) {
+  // per-depth launches over the shard's chains, shaped like the default
+  ChainSet& cs = chain_set(P, MT, ITEM_BYTES, false, lo, hi);
+  LaunchShape L;
+  set_shape<MT>(P, L, 0, ITEM_BYTES, 1, 0, false);
+  L.stage = std::max(L.stage, cs.stage_bytes);
+  gather_native(c.s, c.pperm, c.x, nullptr, c.nv_tiles, c.Nv, c.R, MT, c.scale, c.st, pad_lo, pad_hi);
+  if (adjoint)   // the skeleton vectors of the other shards' rows read as zero
+    HB_CUDA(cudaMemsetAsync(c.xh, 0, (size_t)std::max<long long>(xh_tiles, 1) * MT * 1024, c.st));
+  if (cs.depth_grid != L.grid) build_depth_streams(cs, L.grid);
+  for (const DepthStreams& ds : cs.depth_streams) {
+    if (ds.grid == 0) continue;
+    StepArgs args{ds.d_items, ds.d_off, c.F, c.x, c.xh, c.u, c.pperm, c.Nv, c.R, L.stages, L.stage, c.budget,
+                  c.err, 0};
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ds.grid);
+    cfg.blockDim = dim3(NWARP * 32);
+    cfg.dynamicSmemBytes = L.smem;
+    cfg.stream = c.st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    HB_CUDA(cudaLaunchKernelEx(&cfg, bf_step_kernel<MT>, args));
+  }
+}
+
+void flow_launch_shard(void* plan, const uint4* F, const double2* s, double scale, uint4* x, uint4* xh,
+                       long long xh_tiles, double2* u, const long long* pperm, long long Nv, long long nv_tiles,
+                       int R, long long row_lo, long long row_hi, long long pad_lo, long long pad_hi, bool adjoint,
+                       int* err, long long budget, cudaStream_t st) {
+  FlowPlan* P = static_cast<FlowPlan*>(plan);
+  if (P->terms.empty()) return;
+  const int MT = (R + 15) / 16;
+  const LaunchCtx c{F, s, scale, x, nullptr, nullptr, nullptr, xh, u, pperm, Nv, nv_tiles, R, nullptr, nullptr,
+                    err, budget, false, st};
+  if (MT == 1) launch_shard_mt<1>(P, c, row_lo, row_hi, pad_lo, pad_hi, adjoint, xh_tiles);
+  else if (MT == 2) launch_shard_mt<2>(P, c, row_lo, row_hi, pad_lo, pad_hi, adjoint, xh_tiles);
   else throw Error{HB_ERR_UNSUPPORTED, "the mixed apply takes 1 or 2 m-tiles of 16 right-hand sides per pass"};
 }
 

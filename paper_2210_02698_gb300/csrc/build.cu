@@ -390,6 +390,14 @@ static void make_plans(hb_ctx* c, std::vector<Butterfly>& bfs, const std::vector
   // task plans
   for (int dir = 0; dir < 2; ++dir) {
     std::vector<std::vector<Task>> steps((size_t)Lv + 1);
+    // tree-position rows of each task's row node (the rows it serves; a shard
+    // of the operator computes the tasks whose rows meet its own)
+    std::vector<std::vector<std::pair<long long, long long>>> srows((size_t)Lv + 1);
+    auto push = [&](int step, const Task& tk, long long lo, long long hi) {
+      steps[(size_t)step].push_back(tk);
+      srows[(size_t)step].push_back({lo, hi});
+    };
+    auto node_rows = [&](int level, long long idx) { return std::make_pair(node_lo(c, level, idx), node_hi(c, level, idx)); };
     auto mk = [](long long y_off, int r_out, unsigned char y_buf, unsigned char acc) {
       Task t{};
       t.y_off = y_off;
@@ -409,7 +417,8 @@ static void make_plans(hb_ctx* c, std::vector<Butterfly>& bfs, const std::vector
       tk.x_buf = 0;
       tk.conj_t = (unsigned char)dir;
       tk.kind = 0;
-      steps[0].push_back(tk);
+      // the adjoint's outputs are columns: every shard adds its rows' share
+      push(0, tk, dir == 0 ? p0 : 0, dir == 0 ? p0 + sz : c->Nv);
     }
     for (auto& b : bfs) {
       const int L = b.L;
@@ -426,7 +435,8 @@ static void make_plans(hb_ctx* c, std::vector<Butterfly>& bfs, const std::vector
               tk.x_off[0] = n0;
               tk.r_in[0] = nn;
               tk.kind = 1;
-              steps[0].push_back(tk);
+              const auto rr = node_rows(b.l, b.oi);
+              push(0, tk, rr.first, rr.second);
             }
           } else if (k <= L) {
             const int w = 1 << (L - k);
@@ -441,7 +451,8 @@ static void make_plans(hb_ctx* c, std::vector<Butterfly>& bfs, const std::vector
                 tk.x_off[0] = c1.xh_off;
                 tk.r_in[0] = c1.rank + c2.rank;
                 tk.kind = 2;
-                steps[k].push_back(tk);
+                const auto rr = node_rows(b.l + k, ((long long)b.oi << k) + i);
+                push(k, tk, rr.first, rr.second);
               }
           } else {
             for (int i = 0; i < (1 << L); ++i) {
@@ -454,7 +465,7 @@ static void make_plans(hb_ctx* c, std::vector<Butterfly>& bfs, const std::vector
               tk.x_off[0] = br.xh_off;
               tk.r_in[0] = br.rank;
               tk.kind = 3;
-              steps[L + 1].push_back(tk);
+              push(L + 1, tk, t0, t0 + sz);
             }
           }
         } else {
@@ -470,7 +481,7 @@ static void make_plans(hb_ctx* c, std::vector<Butterfly>& bfs, const std::vector
               tk.r_in[0] = sz;
               tk.conj_t = 1;
               tk.kind = 3;
-              steps[0].push_back(tk);
+              push(0, tk, t0, t0 + sz);
             }
           } else if (k <= L) {
             const int t = L - k + 1;            // adjoint of W^t
@@ -490,7 +501,8 @@ static void make_plans(hb_ctx* c, std::vector<Butterfly>& bfs, const std::vector
                 tk.x_buf = 2;
                 tk.conj_t = 1;
                 tk.kind = 2;
-                steps[k].push_back(tk);
+                const auto rr = node_rows(b.l + t - 1, ((long long)b.oi << (t - 1)) + p);
+                push(k, tk, rr.first, rr.second);
               }
           } else {
             for (int j = 0; j < (1 << L); ++j) {
@@ -504,17 +516,19 @@ static void make_plans(hb_ctx* c, std::vector<Butterfly>& bfs, const std::vector
               tk.r_in[0] = br.rank;
               tk.conj_t = 1;
               tk.kind = 1;
-              steps[L + 1].push_back(tk);
+              push(L + 1, tk, 0, c->Nv);   // column outputs: every shard adds its share
             }
           }
         }
       }
     }
     c->tasks_h[dir].clear();
+    c->task_rows[dir].clear();
     std::vector<int> begins;
-    for (auto& s : steps) {
+    for (size_t q = 0; q < steps.size(); ++q) {
       begins.push_back((int)c->tasks_h[dir].size());
-      c->tasks_h[dir].insert(c->tasks_h[dir].end(), s.begin(), s.end());
+      c->tasks_h[dir].insert(c->tasks_h[dir].end(), steps[q].begin(), steps[q].end());
+      c->task_rows[dir].insert(c->task_rows[dir].end(), srows[q].begin(), srows[q].end());
     }
     begins.push_back((int)c->tasks_h[dir].size());
     c->step_begin[dir] = begins;
@@ -596,6 +610,8 @@ static void make_plans(hb_ctx* c, std::vector<Butterfly>& bfs, const std::vector
                 const BlockRec& br = b.lev[k][(size_t)i * w + j];
                 NatTask t = task(br.xh_tile, tiles8(br.rank), k, 2);
                 t.tc_out = (k == b.L);   // lev[L] is read only by the leaf outputs (K^L)
+                t.row_lo = node_lo(c, b.l + k, ((long long)b.oi << k) + i);
+                t.row_hi = node_hi(c, b.l + k, ((long long)b.oi << k) + i);
                 if (k == 0) {
                   const long long leaf = ((long long)b.si << b.L) + j;
                   const int nn = leaf_size(leaf);
@@ -616,6 +632,8 @@ static void make_plans(hb_ctx* c, std::vector<Butterfly>& bfs, const std::vector
         for (long long t = 0; t < nleaf; ++t) {
           const int sz = leaf_size(t);
           NatTask o = task(c->leaf_tile[(size_t)t], tiles8(sz), Lmax + 1, 1);
+          o.row_lo = node_lo(c, Lv, t);
+          o.row_hi = node_hi(c, Lv, t);
           o.terms.push_back(term(nat(leaf_off[(size_t)t], sz, sz, 0, sz, 0), c->leaf_tile[(size_t)t], tiles8(sz), 0));
           // terms in the order their inputs are produced (HODBF level Lv,
           // whose K^L input is written at depth 0, first): a dataflow launch
@@ -639,6 +657,8 @@ static void make_plans(hb_ctx* c, std::vector<Butterfly>& bfs, const std::vector
             const int sz = leaf_size(leaf);
             NatTask t = task(br.xh_tile, tiles8(br.rank), 0, 2);
             t.tc_out = (b.L == 0);   // lev[0] is read only by the leaf outputs (V^0^H)
+            t.row_lo = node_lo(c, b.l + b.L, ((long long)b.oi << b.L) + i);
+            t.row_hi = node_hi(c, b.l + b.L, ((long long)b.oi << b.L) + i);
             t.terms.push_back(term(nat(b.kl_off[(size_t)i], sz, br.rank, 0, sz, 0), c->leaf_tile[(size_t)leaf],
                                    tiles8(sz), 0));
             nt.push_back(std::move(t));
@@ -658,6 +678,8 @@ static void make_plans(hb_ctx* c, std::vector<Butterfly>& bfs, const std::vector
                 const BlockRec& o2 = b.lev[tl - 1][q1 + 1];
                 NatTask t = task(o1.xh_tile, tiles8(o1.rank) + tiles8(o2.rank), d, 2);
                 t.tc_out = (tl == 1);   // writes lev[0], read only by the leaf outputs
+                t.row_lo = node_lo(c, b.l + tl - 1, ((long long)b.oi << (tl - 1)) + p);
+                t.row_hi = node_hi(c, b.l + tl - 1, ((long long)b.oi << (tl - 1)) + p);
                 for (int cc = 0; cc < 2; ++cc) {
                   const BlockRec& br = b.lev[tl][(size_t)(2 * p + cc) * w + j];
                   t.terms.push_back(term(nat(br.f_off, br.rank, o1.rank, o2.rank, br.rank, 0), br.xh_tile,
@@ -671,6 +693,8 @@ static void make_plans(hb_ctx* c, std::vector<Butterfly>& bfs, const std::vector
         for (long long t = 0; t < nleaf; ++t) {
           const int sz = leaf_size(t);
           NatTask o = task(c->leaf_tile[(size_t)t], tiles8(sz), Lmax + 1, 1);
+          o.row_lo = 0;   // column outputs: every shard adds its rows' share
+          o.row_hi = c->Nv;
           o.terms.push_back(term(nat(leaf_off[(size_t)t], sz, sz, 0, sz, 0), c->leaf_tile[(size_t)t], tiles8(sz), 0));
           for (int l = Lv; l >= 1; --l) {   // inputs in the order they are produced (as above)
             const long long si = t >> (Lv - l);

@@ -8,7 +8,9 @@
 #include <cstdint>
 #include <cstdio>
 #include <functional>
+#include <map>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/hb.h"
@@ -158,6 +160,7 @@ struct NatTask {
   int y_buf;
   int ng;                // n-tiles per group of its blocks
   bool tc_out = false;
+  long long row_lo = 0, row_hi = 0;   // tree-position rows of its row node (a shard runs the tasks meeting its rows)
   std::vector<NatTerm> terms;
 };
 
@@ -268,6 +271,7 @@ struct hb_ctx {
   // apply plans: steps[0] forward, steps[1] adjoint; each step = task range
   std::vector<int> step_begin[2];
   std::vector<hb::Task> tasks_h[2];
+  std::vector<std::pair<long long, long long>> task_rows[2];   // tree-position rows each task serves
   hb::Task* d_tasks[2] = {nullptr, nullptr};
   void* flow_plan[2] = {nullptr, nullptr};  // mixed apply plans (bf_mma.cu)
   int* h_err = nullptr;                    // mapped pinned error word of bounded device waits
@@ -309,6 +313,9 @@ struct hb_ctx {
   // hb_record_id_blocks: blocks per butterfly level to keep, and the kept ones
   int id_rec_per_level = 0;
   std::vector<hb::IdRecord> id_recs;
+
+  // shards (hb_apply_shard*): filtered FP64 step lists by (direction, rows)
+  std::map<std::tuple<int, long long, long long>, void*> shard_cache;
 
   // timing
   bool timing = false;
@@ -357,9 +364,20 @@ void tc_plan_free(void* plan);
 void tc_leaf_launch(void* plan, int MT, const void* F, const uint4* x, const uint4* xh, double2* u,
                     const long long* pperm, long long Nv, int R, int* err, long long budget, cudaStream_t st);
 void gather_native(const double2* s, const long long* pperm, uint4* x, uint4* x_tc, long long nv_tiles, long long Nv,
-                   int R, int MT, double scale, cudaStream_t st);
+                   int R, int MT, double scale, cudaStream_t st, long long win_lo = 0,
+                   long long win_hi = (1LL << 62));
 void apply_bf(hb_ctx* c, const double2* s, double2* u, int nrhs, int adjoint, int precision,
               cudaStream_t st);
+// shards of the apply (apply.cu): rank `rank` of `nranks` owns node `rank` of
+// level log2(nranks) of the cluster tree
+void shard_rows(const hb_ctx* c, int nranks, int rank, long long* lo, long long* hi);
+void apply_bf_shard(hb_ctx* c, const double2* s, double2* u, int nrhs, int adjoint, int precision, int nranks,
+                    int rank, cudaStream_t st);
+void shard_cache_free(hb_ctx* c);
+void flow_launch_shard(void* plan, const uint4* F, const double2* s, double scale, uint4* x, uint4* xh,
+                       long long xh_tiles, double2* u, const long long* pperm, long long Nv, long long nv_tiles,
+                       int R, long long row_lo, long long row_hi, long long pad_lo, long long pad_hi, bool adjoint,
+                       int* err, long long budget, cudaStream_t st);
 // inclusion.cu
 void curve_set(hb_ctx* c, const double* centers, const double* lengths, const double* n_seg, long long ns);
 void curve_free(hb_ctx* c);
