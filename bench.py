@@ -258,7 +258,7 @@ def run_ours(args):
     build.build()
     w = W.WORKLOADS[args.workload]
     tab = load_tables(w)
-    tune = {"tuned": 1, "depth": 0, "dataflow": 2, "tc_leaf": 3}[args.shape]
+    tune = {"tuned": 1, "depth": 0, "dataflow": 2, "tc_leaf": 3, "cones": 4}[args.shape]
     op = binding.Operator(w.N, tab["nodes"], tab["tau2"], tab["v0"], tab["v1"], w.n_cells(), w.omega,
                           eps=w.eps, leaf=w.leaf, chi=w.chi, precision=binding.HB_MIXED_BF16X3, autotune=tune)
     t0 = time.perf_counter()
@@ -480,8 +480,14 @@ def run_ours(args):
                           "butterfly level)",
                        0: "butterfly step kernels of one apply (one launch per dependency depth)",
                        2: "butterfly step kernels of one apply (one launch per dependency depth; the leaf "
-                          "outputs on the tcgen05 tensor-core kernel)"}[shape["mode"]]
-        launches = passes * (1 if shape["mode"] == 1 else 1 + info["levels"] + 1)
+                          "outputs on the tcgen05 tensor-core kernel)",
+                       3: "butterfly step kernels of one apply (the first four butterfly levels as cones in "
+                          "one launch, then one launch per dependency depth)",
+                       4: "butterfly step kernels of one apply (cone launch, one launch per remaining depth, "
+                          "the leaf outputs on the tcgen05 tensor-core kernel)"}[shape["mode"]]
+        ndepth = info["levels"] + 1
+        launches = passes * {1: 1, 0: 1 + ndepth, 2: 1 + ndepth,
+                             3: 2 + max(0, ndepth - 4), 4: 2 + max(0, ndepth - 4)}[shape["mode"]]
         achieved = alg_bytes / (step_ms * 1e-3) / 1e9
         value = Nv * R * world / (ms * 1e-3)
         nc = cores()
@@ -596,7 +602,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(W.WORKLOADS))
     ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU oracle leg (profiling runs)")
-    ap.add_argument("--shape", default="tuned", choices=["tuned", "dataflow", "depth", "tc_leaf"],
+    ap.add_argument("--shape", default="tuned", choices=["tuned", "dataflow", "depth", "tc_leaf", "cones"],
                     help="launch shape of the mixed apply: autotuned (default), the persistent dataflow "
                          "launch, one launch per dependency depth, or that with the leaf outputs on the "
                          "tcgen05 tensor-core kernel")

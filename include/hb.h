@@ -92,7 +92,9 @@ typedef struct {
  * one launch per dependency depth, 16 KB items); 1 = the first
  * mixed apply of each direction and m-tile count (16 right-hand sides per
  * m-tile) times every candidate shape on the caller's stream (one launch per
- * dependency depth at 16 KB or 8 KB items; one persistent launch at 16 KB or
+ * dependency depth at 16 KB or 8 KB items, with or without the cone launch
+ * of the first butterfly levels and the tcgen05 leaf kernel; one persistent
+ * launch at 16 KB or
  * 8 KB items, placement slack 16, 48 or 128 cost units, 1 or 4 chains per
  * flag publication; each a full apply, best of three) and keeps the fastest
  * (hb_launch_shape reports it).  That first apply then blocks the host for
@@ -101,7 +103,11 @@ typedef struct {
  * persistent dataflow launch (16 KB items, slack 48, one chain per
  * publication).  3 = one launch per dependency depth with the leaf outputs
  * on the 5th-generation tensor cores (tcgen05.mma, accumulators in tensor
- * memory; the autotuner's candidates include this shape too). */
+ * memory; the autotuner's candidates include this shape too).  4 = the
+ * first four butterfly levels of every butterfly as "cones" in one launch
+ * (a CTA takes whole cones - forward: one column group, adjoint: one row
+ * group, closed under the dependencies of those levels - and separates their
+ * levels with bounded CTA barriers), then one launch per remaining depth. */
 typedef struct {
   double eps;
   int leaf;
@@ -353,8 +359,9 @@ hb_status hb_fp64_fma_peak(double* tflops, void* stream);
  * per pass, 2: up to 32): *mode = 0 for a gather plus one launch per
  * dependency depth, 1 for one persistent dataflow launch (the gather
  * inside), 2 for a gather plus one launch per depth with the leaf outputs
- * on the tcgen05 tensor-core kernel, -1 if no apply has run yet at that
- * m-tile count; *item_bytes the
+ * on the tcgen05 tensor-core kernel, 3 for the cone launch then one launch
+ * per remaining depth, 4 for that with the tcgen05 leaf kernel, -1 if no
+ * apply has run yet at that m-tile count; *item_bytes the
  * item size the accumulation chains are cut to, *stages the shared-memory
  * ring stages per warp, *pub_batch the chains a dataflow warp publishes
  * together, *slack the dataflow placement's margin between a producer's

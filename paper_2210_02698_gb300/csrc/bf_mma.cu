@@ -281,7 +281,13 @@ __device__ __forceinline__ void zero_acc(float (&acc)[NTW][MT][8]) {
 }
 
 // ------------------------------------------------------------- kernel ----
-template <int MT>
+// CONES: the launch runs cones of butterfly levels (a CTA takes whole cones;
+// within a cone the level of every warp's items is separated by a barrier
+// record, flags & 8).  At a barrier record every lane fences its stores for
+// the async proxy, the warp arrives on the CTA's barrier and waits for the
+// other warps (bounded); the input runs of items issued behind a barrier not
+// yet passed go out once it is.
+template <int MT, bool CONES>
 __global__ void __launch_bounds__(NWARP * 32, 1) bf_step_kernel(StepArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t full[NWARP][MAX_STAGES];
@@ -297,15 +303,31 @@ __global__ void __launch_bounds__(NWARP * 32, 1) bf_step_kernel(StepArgs a) {
   WItem* sl = slot[warp];
 
   __shared__ uint64_t never;   // failure-detection self-test: nothing arrives on it
+  __shared__ uint64_t cbar[2];   // cone level barriers (CONES), used alternately
   if (lane == 0) {
     for (int s = 0; s < nst; ++s) mbar_init(&bar[s], 1);
     if (warp == 0) mbar_init(&never, 1);
+    if (CONES && warp == 0) {
+      mbar_init(&cbar[0], NWARP);
+      mbar_init(&cbar[1], NWARP);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  __syncwarp();
+  if constexpr (CONES) __syncthreads();
+  else __syncwarp();
+  // barrier records issued / passed, and for each stage the barriers that
+  // must be passed before its input run goes out (pending stages only)
+  int bar_issued = 0, bar_passed = 0;
+  unsigned pend = 0;
+  int ep[MAX_STAGES];
+#pragma unroll
+  for (int s = 0; s < MAX_STAGES; ++s) ep[s] = 0;
   const long long deadline = clock64() + a.budget;
   const uint64_t pol_f = policy_evict_first(), pol_v = policy_evict_last();
-  if (a.selftest && blockIdx.x == 0 && warp == 0) {
+  // failure-detection self-test: the first warp also waits, through the
+  // same bounded wait, on a barrier nothing completes (with cones after its
+  // stream, since the other warps of its CTA wait for it at every level)
+  if (!CONES && a.selftest && blockIdx.x == 0 && warp == 0) {
     const bool ok = mbar_wait_until(&never, 0u, deadline);
     if (lane == 0 && !ok) *reinterpret_cast<volatile int*>(a.err) = 1;
     __syncwarp();
@@ -345,6 +367,21 @@ __global__ void __launch_bounds__(NWARP * 32, 1) bf_step_kernel(StepArgs a) {
       __syncwarp();
       if (q >= 32) load_win((q >> 5) + 1);
     }
+    bool x_now = with_x;
+    if constexpr (CONES) {
+      // every lane tracks the barrier records (warp-uniform)
+      const int4 hi = recs[warp][q & 31][1];
+      if ((hi.z >> 24) & 8) {
+        ++bar_issued;
+      } else if (bar_issued > bar_passed) {
+        x_now = false;
+        const int ks = hi.z & 0xffff;
+        if (ks) {
+          pend |= 1u << s;
+          ep[s] = bar_issued;
+        }
+      }
+    }
     if (lane == 0) {
       const int4 lo = recs[warp][q & 31][0], hi = recs[warp][q & 31][1];
       int4* d = reinterpret_cast<int4*>(&sl[s]);
@@ -355,10 +392,15 @@ __global__ void __launch_bounds__(NWARP * 32, 1) bf_step_kernel(StepArgs a) {
       mbar_expect_tx(&bar[s], f_bytes(w) + x_bytes(w));
       if (w.ks) {
         tma_load_1d(st, a.F + w.f_tile * 32, f_bytes(w), &bar[s], pol_f);
-        if (with_x)
+        if (x_now)
           tma_load_1d(st + f_bytes(w), buf(w.x_buf) + w.x_tile * (MT * 64), x_bytes(w), &bar[s], pol_v);
       }
     }
+  };
+  auto issue_x = [&](int s) {   // lane 0: the deferred input run of stage s
+    const WItem& w = sl[s];
+    tma_load_1d(ring + (size_t)s * a.stage_bytes + f_bytes(w), buf(w.x_buf) + w.x_tile * (MT * 64), x_bytes(w),
+                &bar[s], pol_v);
   };
 
   // prologue: factor runs first, input runs once the previous depth is visible
@@ -369,9 +411,7 @@ __global__ void __launch_bounds__(NWARP * 32, 1) bf_step_kernel(StepArgs a) {
     asm volatile("fence.proxy.async.global;" ::: "memory");
     for (long long q = 0; q < pro; ++q) {
       const WItem& w = sl[q];
-      if (w.ks)
-        tma_load_1d(ring + (size_t)q * a.stage_bytes + f_bytes(w), buf(w.x_buf) + w.x_tile * (MT * 64), x_bytes(w),
-                    &bar[q], pol_v);
+      if (w.ks && !((pend >> q) & 1u)) issue_x((int)q);
     }
   }
   __syncwarp();
@@ -386,6 +426,32 @@ __global__ void __launch_bounds__(NWARP * 32, 1) bf_step_kernel(StepArgs a) {
     const WItem& w = sl[s];
     const int flags = w.flags, ntl = w.ntl, ks = w.ks;
     const uint4* st = reinterpret_cast<const uint4*>(ring + (size_t)s * a.stage_bytes);
+    if constexpr (CONES) {
+      if (flags & 8) {
+        // the warp's stores of this level reach the async proxy, then every
+        // warp of the CTA has finished the level
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        __syncwarp();
+        uint64_t* cb = &cbar[bar_passed & 1];
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(cb)) : "memory");
+        const bool okb = mbar_wait_until(cb, (uint32_t)((bar_passed >> 1) & 1), deadline);
+        ++bar_passed;
+        // deferred input runs now allowed (issued even after a timeout: in bounds)
+        unsigned go = 0;
+#pragma unroll
+        for (int t = 0; t < MAX_STAGES; ++t)
+          if (t < nst && ((pend >> t) & 1u) && ep[t] <= bar_passed) go |= 1u << t;
+        if (lane == 0)
+          for (int t = 0; t < nst; ++t)
+            if ((go >> t) & 1u) issue_x(t);
+        pend &= ~go;
+        if (!__all_sync(0xffffffffu, okb)) break;
+        __syncwarp();
+        if (i + nst < n) issue(s, i + nst, true);
+        __syncwarp();
+        continue;
+      }
+    }
     if (flags & 1) zero_acc<MT>(acc);
     if (ks > 0) item_mma<MT>(st, st + ntl * ks * 32, ks, ntl, lane, acc);
     if (flags & 2) {
@@ -402,11 +468,18 @@ __global__ void __launch_bounds__(NWARP * 32, 1) bf_step_kernel(StepArgs a) {
     // a wait ran out: report it, let the copies in flight land, stop
     if (lane == 0) {
       *reinterpret_cast<volatile int*>(a.err) = 1;
+      for (int t = 0; t < nst; ++t)
+        if ((pend >> t) & 1u) issue_x(t);   // in bounds: every stage completes
       const long long last = (i + nst < n) ? i + nst : n;
       const long long drain = a.budget > (1LL << 31) ? a.budget : (1LL << 31);
       for (long long j = i; j < last; ++j)
         mbar_wait_until(&bar[j % nst], (uint32_t)((j / nst) & 1), clock64() + drain);
     }
+    __syncwarp();
+  }
+  if (CONES && a.selftest && blockIdx.x == 0 && warp == 0) {
+    const bool ok = mbar_wait_until(&never, 0u, clock64() + a.budget);
+    if (lane == 0 && !ok) *reinterpret_cast<volatile int*>(a.err) = 1;
     __syncwarp();
   }
   if (lane == 0) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
@@ -891,6 +964,7 @@ struct LaunchShape {
   int pub = 2;
   int slack = 48;        // dataflow placement: cost units between a producer's finish and its consumer
   bool tc = false;       // mode 0: the leaf outputs on the tensor-core leaf kernel
+  bool cones = false;    // mode 0: the first butterfly levels as cones in one launch
   size_t smem = 0;
   double tuned_ms = 0;   // the chosen candidate's time (0: not tuned)
   int candidates = 0;    // candidates the autotuner timed
@@ -900,8 +974,13 @@ struct LaunchShape {
 struct ChainSet {
   int stage_bytes = 512;                                   // largest item (factor run + input run)
   std::vector<std::vector<std::vector<WItem>>> by_depth;   // [depth][chain] -> items
+  std::vector<std::vector<std::pair<long long, int>>> cone_of;   // [depth][chain] -> (cone, level)
   int depth_grid = 0;
   std::vector<DepthStreams> depth_streams;                 // mode 0: one stream set per depth
+  int cone_grid = 0;
+  DepthStreams cone_streams;                               // mode 0 with cones: the cone launch
+  int depth_grid_c = 0;
+  std::vector<DepthStreams> depth_streams_c;               // mode 0 with cones: the other chains per depth
   int flow_grid = 0;
   std::map<int, DepthStreams> flow_streams;                // mode 1: all depths in one stream set, per slack
 };
@@ -912,6 +991,7 @@ struct ChainSet {
 struct FlowPlan {
   std::vector<std::vector<std::vector<WItem>>> terms;   // [depth][group chain] -> uncut terms
   std::vector<std::vector<std::pair<long long, long long>>> rows;   // [depth][group chain] -> tree rows it serves
+  std::vector<std::vector<std::pair<long long, int>>> cone;         // [depth][group chain] -> (cone, level)
   long long xh_tiles = 0;                               // row tiles the plan writes in xh
   std::map<std::tuple<int, int, int, long long, long long>, ChainSet> sets;   // (MT, item bytes, tc, rows) -> chains
   LaunchShape shape[3];
@@ -933,6 +1013,7 @@ void flow_plan_build(const std::vector<NatTask>& lt, void** plan_out) {
     for (const NatTask& L : lt) maxd = std::max(maxd, L.depth);
     P->terms.assign((size_t)(maxd + 1), {});
     P->rows.assign((size_t)(maxd + 1), {});
+    P->cone.assign((size_t)(maxd + 1), {});
     for (const NatTask& L : lt) {
       if (L.nt <= 0) continue;
       if (L.ng < 1 || L.ng > NTW) throw Error{HB_ERR_UNSUPPORTED, "n-tile group larger than the accumulators"};
@@ -964,6 +1045,7 @@ void flow_plan_build(const std::vector<NatTask>& lt, void** plan_out) {
         }
         P->terms[(size_t)L.depth].push_back(std::move(ch));
         P->rows[(size_t)L.depth].push_back({L.row_lo, L.row_hi});
+        P->cone[(size_t)L.depth].push_back({L.cone, L.cone_level});
       }
     }
     for (const NatTask& L : lt)
@@ -1015,6 +1097,7 @@ static ChainSet& chain_set(FlowPlan* P, int MT, int item_bytes, bool tc, long lo
   ChainSet cs;
   const size_t nd = P->terms.size() - (tc ? 1 : 0);
   cs.by_depth.assign(nd, {});
+  cs.cone_of.assign(nd, {});
   for (size_t d = 0; d < nd; ++d)
     for (size_t q = 0; q < P->terms[d].size(); ++q) {
       const auto& tch = P->terms[d][q];
@@ -1023,6 +1106,7 @@ static ChainSet& chain_set(FlowPlan* P, int MT, int item_bytes, bool tc, long lo
       std::vector<WItem> ch;
       cut_chain(tch, MT, item_bytes, tc, ch, cs.stage_bytes);
       cs.by_depth[d].push_back(std::move(ch));
+      cs.cone_of[d].push_back(P->cone[d][q]);
     }
   return P->sets.emplace(key, std::move(cs)).first->second;
 }
@@ -1037,6 +1121,11 @@ static void free_set(ChainSet& cs) {
   for (DepthStreams& d : cs.depth_streams) free_streams(d);
   cs.depth_streams.clear();
   cs.depth_grid = 0;
+  free_streams(cs.cone_streams);
+  cs.cone_grid = 0;
+  for (DepthStreams& d : cs.depth_streams_c) free_streams(d);
+  cs.depth_streams_c.clear();
+  cs.depth_grid_c = 0;
   for (auto& kv : cs.flow_streams) free_streams(kv.second);
   cs.flow_streams.clear();
   cs.flow_grid = 0;
@@ -1085,19 +1174,22 @@ static DepthStreams upload_streams(const std::vector<std::vector<const std::vect
 // Mode 0: deal every depth's chains over grid x NWARP warp streams, longest
 // chain (in factor tiles, plus a fixed cost per item) first, to the stream
 // with the least work so far.
-static void build_depth_streams(ChainSet& cs, int grid) {
-  for (DepthStreams& d : cs.depth_streams) free_streams(d);
-  cs.depth_streams.clear();
+static void build_depth_streams(ChainSet& cs, int grid, bool skip_cones = false) {
+  std::vector<DepthStreams>& out = skip_cones ? cs.depth_streams_c : cs.depth_streams;
+  for (DepthStreams& d : out) free_streams(d);
+  out.clear();
   const int ns = grid * NWARP;
-  for (const auto& chains : cs.by_depth) {
-    if (chains.empty()) {
-      cs.depth_streams.push_back(DepthStreams{});
+  for (size_t dd = 0; dd < cs.by_depth.size(); ++dd) {
+    const auto& chains = cs.by_depth[dd];
+    std::vector<size_t> order;
+    for (size_t c = 0; c < chains.size(); ++c)
+      if (!skip_cones || cs.cone_of[dd][c].first < 0) order.push_back(c);
+    if (order.empty()) {
+      out.push_back(DepthStreams{});
       continue;
     }
     std::vector<long long> cost(chains.size());
     for (size_t c = 0; c < chains.size(); ++c) cost[c] = chain_cost(chains[c]);
-    std::vector<size_t> order(chains.size());
-    std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
     using Load = std::pair<long long, int>;
     std::priority_queue<Load, std::vector<Load>, std::greater<Load>> pq;
@@ -1110,9 +1202,72 @@ static void build_depth_streams(ChainSet& cs, int grid) {
       l.first += cost[c];
       pq.push(l);
     }
-    cs.depth_streams.push_back(upload_streams(per, grid));
+    out.push_back(upload_streams(per, grid));
   }
-  cs.depth_grid = grid;
+  (skip_cones ? cs.depth_grid_c : cs.depth_grid) = grid;
+}
+
+// Mode 0 with cones: the chains of every cone (the first butterfly levels,
+// tasks with cone >= 0) in one launch.  Whole cones go to CTAs (largest
+// first to the least-loaded CTA); within a CTA each cone's levels are dealt
+// to its NWARP warps level by level (largest chain first to the warp with
+// the least work in that level), and every warp gets a barrier record after
+// each level but the cone's last, so all warps of the CTA hold the same
+// barriers in the same order.
+static void build_cone_streams(ChainSet& cs, int grid) {
+  free_streams(cs.cone_streams);
+  static const std::vector<WItem> barrier_rec = [] {
+    WItem w{};
+    w.flags = 8;
+    return std::vector<WItem>{w};
+  }();
+  std::map<long long, std::vector<std::vector<const std::vector<WItem>*>>> cones;   // cone -> level -> chains
+  std::map<long long, long long> cone_cost;
+  for (size_t d = 0; d < cs.by_depth.size(); ++d)
+    for (size_t q = 0; q < cs.by_depth[d].size(); ++q) {
+      const auto& ci = cs.cone_of[d][q];
+      if (ci.first < 0) continue;
+      auto& lv = cones[ci.first];
+      if ((int)lv.size() <= ci.second) lv.resize((size_t)ci.second + 1);
+      lv[(size_t)ci.second].push_back(&cs.by_depth[d][q]);
+      cone_cost[ci.first] += chain_cost(cs.by_depth[d][q]);
+    }
+  std::vector<long long> ids;
+  for (const auto& kv : cones) ids.push_back(kv.first);
+  std::stable_sort(ids.begin(), ids.end(), [&](long long x, long long y) { return cone_cost[x] > cone_cost[y]; });
+  using Load = std::pair<long long, int>;
+  std::priority_queue<Load, std::vector<Load>, std::greater<Load>> pq;
+  for (int b = 0; b < grid; ++b) pq.push({0, b});
+  std::vector<std::vector<long long>> of_cta((size_t)grid);
+  for (long long id : ids) {
+    Load l = pq.top();
+    pq.pop();
+    of_cta[(size_t)l.second].push_back(id);
+    l.first += cone_cost[id];
+    pq.push(l);
+  }
+  std::vector<std::vector<const std::vector<WItem>*>> per((size_t)grid * NWARP);
+  for (int b = 0; b < grid; ++b)
+    for (long long id : of_cta[(size_t)b]) {
+      const auto& lv = cones[id];
+      for (size_t k = 0; k < lv.size(); ++k) {
+        std::vector<const std::vector<WItem>*> chs = lv[k];
+        std::stable_sort(chs.begin(), chs.end(),
+                         [](const std::vector<WItem>* x, const std::vector<WItem>* y) { return chain_cost(*x) > chain_cost(*y); });
+        long long load[NWARP] = {};
+        for (const auto* c : chs) {
+          int wmin = 0;
+          for (int w = 1; w < NWARP; ++w)
+            if (load[w] < load[wmin]) wmin = w;
+          per[(size_t)b * NWARP + wmin].push_back(c);
+          load[wmin] += chain_cost(*c);
+        }
+        if (k + 1 < lv.size())
+          for (int w = 0; w < NWARP; ++w) per[(size_t)b * NWARP + w].push_back(&barrier_rec);
+      }
+    }
+  cs.cone_streams = upload_streams(per, grid);
+  cs.cone_grid = grid;
 }
 
 // Mode 1: one stream set over all depths, placed by simulating the schedule.
@@ -1214,16 +1369,20 @@ static void build_flow_streams(ChainSet& cs, int grid, int slack, long long xh_t
 }
 
 template <int MT>
-static void set_shape(FlowPlan* P, LaunchShape& L, int mode, int item_bytes, int pub, int slack, bool tc) {
+static void set_shape(FlowPlan* P, LaunchShape& L, int mode, int item_bytes, int pub, int slack, bool tc,
+                      bool cones = false) {
   int dev = 0, nsm = 0, optin = 0;
   HB_CUDA(cudaGetDevice(&dev));
   HB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   HB_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   if (tc && mode != 0) throw Error{HB_ERR_UNSUPPORTED, "the tensor-core leaf kernel runs with one launch per depth"};
+  if (cones && mode != 0) throw Error{HB_ERR_UNSUPPORTED, "cones run with one launch per depth"};
   ChainSet& cs = chain_set(P, MT, item_bytes, tc);
   L.tc = tc;
+  L.cones = cones;
   cudaFuncAttributes fa{};
-  const void* k = mode == 0 ? (const void*)bf_step_kernel<MT> : (const void*)bf_flow_kernel<MT>;
+  const void* k = mode == 0 ? (cones ? (const void*)bf_step_kernel<MT, true> : (const void*)bf_step_kernel<MT, false>)
+                            : (const void*)bf_flow_kernel<MT>;
   HB_CUDA(cudaFuncGetAttributes(&fa, k));
   L.mode = mode;
   L.item_bytes = item_bytes;
@@ -1236,6 +1395,9 @@ static void set_shape(FlowPlan* P, LaunchShape& L, int mode, int item_bytes, int
   L.smem = (size_t)NWARP * L.stages * L.stage;
   // the kernel may take any size up to the opt-in limit (both directions' plans share it)
   HB_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, avail));
+  if (cones)   // the per-depth launches after the cone launch
+    HB_CUDA(cudaFuncSetAttribute((const void*)bf_step_kernel<MT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 avail));
   int per_sm = 0;
   HB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NWARP * 32, L.smem));
   if (per_sm < 1) throw Error{HB_ERR_UNSUPPORTED, "step kernel does not fit on an SM"};
@@ -1270,8 +1432,38 @@ static void launch_shape(FlowPlan* P, const LaunchShape& L, const LaunchCtx& c,
   ChainSet& cs = chain_set(P, MT, L.item_bytes, L.tc);
   if (L.mode == 0) {
     gather_native(c.s, c.pperm, c.x, L.tc ? c.x_tc : nullptr, c.nv_tiles, c.Nv, c.R, MT, c.scale, c.st);
-    if (cs.depth_grid != L.grid) build_depth_streams(cs, L.grid);
     bool first = true;   // the timer brackets all depth launches (PDL stays intact)
+    auto launch = [&](const DepthStreams& ds, bool cone_kernel) {
+      StepArgs args{ds.d_items, ds.d_off, c.F, c.x, c.xh, c.u, c.pperm, c.Nv, c.R, L.stages, L.stage, c.budget,
+                    c.err, c.selftest ? 1 : 0};
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(ds.grid);
+      cfg.blockDim = dim3(NWARP * 32);
+      cfg.dynamicSmemBytes = L.smem;
+      cfg.stream = c.st;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      attr[0].val.programmaticStreamSerializationAllowed = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      if (first) timer(0, true);
+      first = false;
+      if (cone_kernel) HB_CUDA(cudaLaunchKernelEx(&cfg, bf_step_kernel<MT, true>, args));
+      else HB_CUDA(cudaLaunchKernelEx(&cfg, bf_step_kernel<MT, false>, args));
+    };
+    if (L.cones) {
+      if (cs.cone_grid != L.grid) build_cone_streams(cs, L.grid);
+      if (cs.depth_grid_c != L.grid) build_depth_streams(cs, L.grid, true);
+      launch(cs.cone_streams, true);
+      for (const DepthStreams& ds : cs.depth_streams_c)
+        if (ds.grid) launch(ds, false);
+      if (L.tc) {
+        tc_leaf_launch(c.tc_plan, MT, c.F_tc, c.x_tc, c.xh, c.u, c.pperm, c.Nv, c.R, c.err, c.budget, c.st);
+      }
+      timer(0, false);
+      return;
+    }
+    if (cs.depth_grid != L.grid) build_depth_streams(cs, L.grid);
     for (const DepthStreams& ds : cs.depth_streams) {
       if (ds.grid == 0) continue;
       StepArgs args{ds.d_items, ds.d_off, c.F, c.x, c.xh, c.u, c.pperm, c.Nv, c.R, L.stages, L.stage, c.budget,
@@ -1288,7 +1480,7 @@ static void launch_shape(FlowPlan* P, const LaunchShape& L, const LaunchCtx& c,
       cfg.numAttrs = 1;
       if (first) timer(0, true);
       first = false;
-      HB_CUDA(cudaLaunchKernelEx(&cfg, bf_step_kernel<MT>, args));
+      HB_CUDA(cudaLaunchKernelEx(&cfg, bf_step_kernel<MT, false>, args));
     }
     if (L.tc) {   // the leaf outputs (the last depth) on the tensor cores
       if (first) timer(0, true);
@@ -1336,11 +1528,13 @@ static void launch_shape(FlowPlan* P, const LaunchShape& L, const LaunchCtx& c,
 template <int MT>
 static void autotune(FlowPlan* P, LaunchShape& L, const LaunchCtx& c) {
   struct Cand {
-    int mode, item_bytes, pub, slack, tc;
+    int mode, item_bytes, pub, slack, tc, cones;
   };
-  const Cand cands[] = {{0, 16384, 1, 0, 0},  {0, 8192, 1, 0, 0},   {0, 16384, 1, 0, 1},  {0, 8192, 1, 0, 1},
-                        {1, 16384, 1, 16, 0}, {1, 16384, 1, 48, 0}, {1, 16384, 1, 128, 0}, {1, 16384, 4, 48, 0},
-                        {1, 8192, 1, 16, 0},  {1, 8192, 1, 48, 0},  {1, 8192, 1, 128, 0}};
+  const Cand cands[] = {{0, 16384, 1, 0, 0, 0},  {0, 8192, 1, 0, 0, 0},   {0, 16384, 1, 0, 1, 0},
+                        {0, 8192, 1, 0, 1, 0},   {0, 16384, 1, 0, 0, 1},  {0, 8192, 1, 0, 0, 1},
+                        {0, 16384, 1, 0, 1, 1},  {1, 16384, 1, 16, 0, 0}, {1, 16384, 1, 48, 0, 0},
+                        {1, 16384, 1, 128, 0, 0}, {1, 16384, 4, 48, 0, 0}, {1, 8192, 1, 16, 0, 0},
+                        {1, 8192, 1, 48, 0, 0},  {1, 8192, 1, 128, 0, 0}};
   cudaEvent_t e0, e1;
   HB_CUDA(cudaEventCreate(&e0));
   HB_CUDA(cudaEventCreate(&e1));
@@ -1352,7 +1546,7 @@ static void autotune(FlowPlan* P, LaunchShape& L, const LaunchCtx& c) {
     for (const Cand& k : cands) {
       LaunchShape T;
       try {
-        set_shape<MT>(P, T, k.mode, k.item_bytes, k.pub, k.slack, k.tc != 0);
+        set_shape<MT>(P, T, k.mode, k.item_bytes, k.pub, k.slack, k.tc != 0, k.cones != 0);
       } catch (const Error&) {
         continue;   // does not fit: not a candidate
       }
@@ -1419,6 +1613,7 @@ static void run_mt(FlowPlan* P, const LaunchCtx& c, int tune, const std::functio
     if (tune == 1 && cap == cudaStreamCaptureStatusNone) autotune<MT>(P, L, c);
     else if (tune == 2) set_shape<MT>(P, L, 1, ITEM_BYTES, 1, 48, false);
     else if (tune == 3) set_shape<MT>(P, L, 0, ITEM_BYTES, 1, 0, true);
+    else if (tune == 4) set_shape<MT>(P, L, 0, ITEM_BYTES, 1, 0, false, true);
     else set_shape<MT>(P, L, 0, ITEM_BYTES, 1, 0, false);
   }
   launch_shape<MT>(P, L, c, timer);
@@ -1464,7 +1659,7 @@ static void launch_shard_mt(FlowPlan* P, const LaunchCtx& c, long long lo, long 
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    HB_CUDA(cudaLaunchKernelEx(&cfg, bf_step_kernel<MT>, args));
+    HB_CUDA(cudaLaunchKernelEx(&cfg, bf_step_kernel<MT, false>, args));
   }
 }
 
@@ -1486,7 +1681,7 @@ void flow_shape(const void* plan, int MT, int* mode, int* item_bytes, int* stage
                 double* tuned_ms, int* candidates) {
   const FlowPlan* P = static_cast<const FlowPlan*>(plan);
   const LaunchShape& L = P->shape[MT];
-  *mode = L.ready ? (L.mode == 0 && L.tc ? 2 : L.mode) : -1;
+  *mode = !L.ready ? -1 : L.mode == 1 ? 1 : L.cones ? (L.tc ? 4 : 3) : (L.tc ? 2 : 0);
   *item_bytes = L.item_bytes;
   *stages = L.stages;
   *pub = L.pub;

@@ -44,6 +44,13 @@ namespace hb {
 #endif
 constexpr int LEAF_NG = HB_LEAF_NG;   // n-tiles per group of the leaf-output tasks (mixed apply)
 constexpr int BLOCK_NG = HB_NG;       // n-tiles per group of the other tasks
+// Cones: levels 0 .. min(L, CONE_M) of every butterfly (forward; adjoint: its
+// first CONE_M + 1 steps) split into groups closed under their dependencies.
+// Forward: level k block (i, j) reads level k - 1 blocks (i/2, 2j), (i/2, 2j+1),
+// so the blocks with j >> (m - k) == c (m = min(L, CONE_M)) need only x and
+// one another.  Adjoint: the step writing level L - d pair (p, .) reads level
+// L - d + 1 blocks (2p + cc, j), so the blocks with row >> (m - d) == a do.
+constexpr int CONE_M = 3;
 
 struct BlockRec {
   int rank = 0;
@@ -589,6 +596,10 @@ static void make_plans(hb_ctx* c, std::vector<Butterfly>& bfs, const std::vector
         return tm;
       };
       std::vector<NatTask> nt;
+      // first cone id of every butterfly: 2^(L - min(L, CONE_M)) cones each
+      std::vector<long long> cone_base(bfs.size() + 1, 0);
+      for (size_t bi = 0; bi < bfs.size(); ++bi)
+        cone_base[bi + 1] = cone_base[bi] + (1LL << (bfs[bi].L - std::min(bfs[bi].L, CONE_M)));
       auto task = [&](long long y_tile, long long ntl, int depth, int y_buf) {
         NatTask t;
         t.y_tile = y_tile;
@@ -612,6 +623,13 @@ static void make_plans(hb_ctx* c, std::vector<Butterfly>& bfs, const std::vector
                 t.tc_out = (k == b.L);   // lev[L] is read only by the leaf outputs (K^L)
                 t.row_lo = node_lo(c, b.l + k, ((long long)b.oi << k) + i);
                 t.row_hi = node_hi(c, b.l + k, ((long long)b.oi << k) + i);
+                {
+                  const int m = std::min(b.L, CONE_M);
+                  if (k <= m) {
+                    t.cone = cone_base[bi] + (j >> (m - k));
+                    t.cone_level = k;
+                  }
+                }
                 if (k == 0) {
                   const long long leaf = ((long long)b.si << b.L) + j;
                   const int nn = leaf_size(leaf);
@@ -659,6 +677,8 @@ static void make_plans(hb_ctx* c, std::vector<Butterfly>& bfs, const std::vector
             t.tc_out = (b.L == 0);   // lev[0] is read only by the leaf outputs (V^0^H)
             t.row_lo = node_lo(c, b.l + b.L, ((long long)b.oi << b.L) + i);
             t.row_hi = node_hi(c, b.l + b.L, ((long long)b.oi << b.L) + i);
+            t.cone = cone_base[bi] + (i >> std::min(b.L, CONE_M));
+            t.cone_level = 0;
             t.terms.push_back(term(nat(b.kl_off[(size_t)i], sz, br.rank, 0, sz, 0), c->leaf_tile[(size_t)leaf],
                                    tiles8(sz), 0));
             nt.push_back(std::move(t));
@@ -680,6 +700,13 @@ static void make_plans(hb_ctx* c, std::vector<Butterfly>& bfs, const std::vector
                 t.tc_out = (tl == 1);   // writes lev[0], read only by the leaf outputs
                 t.row_lo = node_lo(c, b.l + tl - 1, ((long long)b.oi << (tl - 1)) + p);
                 t.row_hi = node_hi(c, b.l + tl - 1, ((long long)b.oi << (tl - 1)) + p);
+                {
+                  const int m = std::min(b.L, CONE_M);
+                  if (d <= m) {
+                    t.cone = cone_base[bi] + (p >> (m - d));
+                    t.cone_level = d;
+                  }
+                }
                 for (int cc = 0; cc < 2; ++cc) {
                   const BlockRec& br = b.lev[tl][(size_t)(2 * p + cc) * w + j];
                   t.terms.push_back(term(nat(br.f_off, br.rank, o1.rank, o2.rank, br.rank, 0), br.xh_tile,

@@ -161,6 +161,11 @@ struct NatTask {
   int ng;                // n-tiles per group of its blocks
   bool tc_out = false;
   long long row_lo = 0, row_hi = 0;   // tree-position rows of its row node (a shard runs the tasks meeting its rows)
+  // cone of the first butterfly levels (forward: blocks of one column group,
+  // adjoint: one row group; closed under the dependencies of those levels):
+  // cone id (-1: none) and the task's level within it
+  long long cone = -1;
+  int cone_level = 0;
   std::vector<NatTerm> terms;
 };
 
