@@ -258,7 +258,7 @@ def run_ours(args):
     build.build()
     w = W.WORKLOADS[args.workload]
     tab = load_tables(w)
-    tune = {"tuned": 1, "depth": 0, "dataflow": 2, "tc_leaf": 3, "cones": 4}[args.shape]
+    tune = {"tuned": 1, "depth": 0, "dataflow": 2, "tc_leaf": 3, "cones": 4, "pairs": 5}[args.shape]
     op = binding.Operator(w.N, tab["nodes"], tab["tau2"], tab["v0"], tab["v1"], w.n_cells(), w.omega,
                           eps=w.eps, leaf=w.leaf, chi=w.chi, precision=binding.HB_MIXED_BF16X3, autotune=tune)
     t0 = time.perf_counter()
@@ -484,10 +484,15 @@ def run_ours(args):
                        3: "butterfly step kernels of one apply (the first four butterfly levels as cones in "
                           "one launch, then one launch per dependency depth)",
                        4: "butterfly step kernels of one apply (cone launch, one launch per remaining depth, "
-                          "the leaf outputs on the tcgen05 tensor-core kernel)"}[shape["mode"]]
+                          "the leaf outputs on the tcgen05 tensor-core kernel)",
+                       5: "butterfly step kernels of one apply (the transfer depths fused in pairs, one launch "
+                          "per pair, then the leaf outputs)",
+                       6: "butterfly step kernels of one apply (the transfer depths fused in pairs; the leaf "
+                          "outputs on the tcgen05 tensor-core kernel)"}[shape["mode"]]
         ndepth = info["levels"] + 1
         launches = passes * {1: 1, 0: 1 + ndepth, 2: 1 + ndepth,
-                             3: 2 + max(0, ndepth - 4), 4: 2 + max(0, ndepth - 4)}[shape["mode"]]
+                             3: 2 + max(0, ndepth - 4), 4: 2 + max(0, ndepth - 4),
+                             5: 2 + (ndepth - 1 + 1) // 2, 6: 2 + (ndepth - 1 + 1) // 2}[shape["mode"]]
         achieved = alg_bytes / (step_ms * 1e-3) / 1e9
         value = Nv * R * world / (ms * 1e-3)
         nc = cores()
@@ -602,7 +607,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(W.WORKLOADS))
     ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU oracle leg (profiling runs)")
-    ap.add_argument("--shape", default="tuned", choices=["tuned", "dataflow", "depth", "tc_leaf", "cones"],
+    ap.add_argument("--shape", default="tuned", choices=["tuned", "dataflow", "depth", "tc_leaf", "cones", "pairs"],
                     help="launch shape of the mixed apply: autotuned (default), the persistent dataflow "
                          "launch, one launch per dependency depth, or that with the leaf outputs on the "
                          "tcgen05 tensor-core kernel")

@@ -107,7 +107,10 @@ typedef struct {
  * first four butterfly levels of every butterfly as "cones" in one launch
  * (a CTA takes whole cones - forward: one column group, adjoint: one row
  * group, closed under the dependencies of those levels - and separates their
- * levels with bounded CTA barriers), then one launch per remaining depth. */
+ * levels with bounded CTA barriers), then one launch per remaining depth.
+ * 5 = the transfer depths fused in pairs (2P, 2P + 1), one launch per pair:
+ * each producer / consumer component of a pair runs on one warp, the
+ * consumers copying their inputs (the warp's own outputs) with cp.async. */
 typedef struct {
   double eps;
   int leaf;
@@ -360,7 +363,8 @@ hb_status hb_fp64_fma_peak(double* tflops, void* stream);
  * dependency depth, 1 for one persistent dataflow launch (the gather
  * inside), 2 for a gather plus one launch per depth with the leaf outputs
  * on the tcgen05 tensor-core kernel, 3 for the cone launch then one launch
- * per remaining depth, 4 for that with the tcgen05 leaf kernel, -1 if no
+ * per remaining depth, 4 for that with the tcgen05 leaf kernel, 5 for the
+ * fused level pairs, 6 for those with the tcgen05 leaf kernel, -1 if no
  * apply has run yet at that m-tile count; *item_bytes the
  * item size the accumulation chains are cut to, *stages the shared-memory
  * ring stages per warp, *pub_batch the chains a dataflow warp publishes

@@ -82,4 +82,20 @@ __device__ __forceinline__ void st_global_hint(uint4* p, const uint4& v, uint64_
                : "memory");
 }
 
+// cp.async (generic proxy, L2 only): 16 bytes global -> shared, grouped by
+// commit_group; wait_pending(n) waits until at most n groups of the thread
+// are still in flight (n > 3 waits as for 3)
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_pending(int n) {
+  switch (n) {
+    case 0: asm volatile("cp.async.wait_group 0;" ::: "memory"); break;
+    case 1: asm volatile("cp.async.wait_group 1;" ::: "memory"); break;
+    case 2: asm volatile("cp.async.wait_group 2;" ::: "memory"); break;
+    default: asm volatile("cp.async.wait_group 3;" ::: "memory"); break;
+  }
+}
+
 }  // namespace hb

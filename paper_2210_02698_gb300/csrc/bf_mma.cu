@@ -287,8 +287,10 @@ __device__ __forceinline__ void zero_acc(float (&acc)[NTW][MT][8]) {
 // the async proxy, the warp arrives on the CTA's barrier and waits for the
 // other warps (bounded); the input runs of items issued behind a barrier not
 // yet passed go out once it is.
-template <int MT, bool CONES>
+template <int MT, int VAR>
 __global__ void __launch_bounds__(NWARP * 32, 1) bf_step_kernel(StepArgs a) {
+  constexpr bool CONES = VAR == 1;   // barrier records between cone levels
+  constexpr bool PAIRS = VAR == 2;   // fused level pairs: items reading this warp's own outputs (flags & 16)
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t full[NWARP][MAX_STAGES];
   __shared__ __align__(16) WItem slot[NWARP][MAX_STAGES];
@@ -322,6 +324,11 @@ __global__ void __launch_bounds__(NWARP * 32, 1) bf_step_kernel(StepArgs a) {
   int ep[MAX_STAGES];
 #pragma unroll
   for (int s = 0; s < MAX_STAGES; ++s) ep[s] = 0;
+  // PAIRS: cp.async groups committed so far, and the group of each stage
+  long long gseq = 0;
+  long long gs[MAX_STAGES];
+#pragma unroll
+  for (int s = 0; s < MAX_STAGES; ++s) gs[s] = -1;
   const long long deadline = clock64() + a.budget;
   const uint64_t pol_f = policy_evict_first(), pol_v = policy_evict_last();
   // failure-detection self-test: the first warp also waits, through the
@@ -355,6 +362,16 @@ __global__ void __launch_bounds__(NWARP * 32, 1) bf_step_kernel(StepArgs a) {
   load_win(1);
   auto f_bytes = [](const WItem& w) { return (uint32_t)w.ntl * (uint32_t)w.ks * 512u; };
   auto x_bytes = [](const WItem& w) { return (uint32_t)w.ks * (uint32_t)(MT * 1024); };
+  // PAIRS, all lanes: the input run of the item in stage s (this warp's own
+  // earlier output, in xh) copied into the stage with cp.async, one group
+  auto own_copy = [&](int s, const WItem& w) {
+    uint4* dst = reinterpret_cast<uint4*>(ring + (size_t)s * a.stage_bytes + f_bytes(w));
+    const uint4* src = a.xh + w.x_tile * (MT * 64);
+    const int chunks = w.ks * MT * 64;
+    for (int c = lane; c < chunks; c += 32) cp_async16(dst + c, src + c);
+    cp_async_commit();
+    gs[s] = gseq++;
+  };
   // all lanes: stage s gets item q; lane 0 stores its record, arms the
   // barrier and fetches the factor run (and the input run when with_x)
   auto issue = [&](int s, long long q, bool with_x) {
@@ -382,6 +399,23 @@ __global__ void __launch_bounds__(NWARP * 32, 1) bf_step_kernel(StepArgs a) {
         }
       }
     }
+    bool own = false;   // PAIRS: the input run is this warp's own output (copied by cp.async)
+    if constexpr (PAIRS) {
+      const int4 hi = recs[warp][q & 31][1];
+      own = ((hi.z >> 24) & 16) != 0 && (hi.z & 0xffff) != 0;
+      if (own) {
+        x_now = false;
+        // the producing items are done once the item `pad` places back is
+        // computed, i.e. when it lies nst or more places back
+        const int dist = (int)((unsigned)hi.w >> 16);
+        if (with_x && dist >= nst) {
+          const WItem& wq = *reinterpret_cast<const WItem*>(recs[warp][q & 31]);
+          own_copy(s, wq);
+        } else {
+          pend |= 1u << s;
+        }
+      }
+    }
     if (lane == 0) {
       const int4 lo = recs[warp][q & 31][0], hi = recs[warp][q & 31][1];
       int4* d = reinterpret_cast<int4*>(&sl[s]);
@@ -389,7 +423,7 @@ __global__ void __launch_bounds__(NWARP * 32, 1) bf_step_kernel(StepArgs a) {
       d[1] = hi;
       const WItem& w = sl[s];
       unsigned char* st = ring + (size_t)s * a.stage_bytes;
-      mbar_expect_tx(&bar[s], f_bytes(w) + x_bytes(w));
+      mbar_expect_tx(&bar[s], f_bytes(w) + (own ? 0u : x_bytes(w)));
       if (w.ks) {
         tma_load_1d(st, a.F + w.f_tile * 32, f_bytes(w), &bar[s], pol_f);
         if (x_now)
@@ -452,6 +486,16 @@ __global__ void __launch_bounds__(NWARP * 32, 1) bf_step_kernel(StepArgs a) {
         continue;
       }
     }
+    if constexpr (PAIRS) {
+      if ((flags & 16) && ks > 0) {
+        if ((pend >> s) & 1u) {   // its producers are done now: copy, then wait for it
+          own_copy(s, w);
+          pend &= ~(1u << s);
+        }
+        cp_async_wait_pending((int)(gseq - 1 - gs[s]));
+        __syncwarp();
+      }
+    }
     if (flags & 1) zero_acc<MT>(acc);
     if (ks > 0) item_mma<MT>(st, st + ntl * ks * 32, ks, ntl, lane, acc);
     if (flags & 2) {
@@ -469,7 +513,7 @@ __global__ void __launch_bounds__(NWARP * 32, 1) bf_step_kernel(StepArgs a) {
     if (lane == 0) {
       *reinterpret_cast<volatile int*>(a.err) = 1;
       for (int t = 0; t < nst; ++t)
-        if ((pend >> t) & 1u) issue_x(t);   // in bounds: every stage completes
+        if (!PAIRS && ((pend >> t) & 1u)) issue_x(t);   // in bounds: every stage completes
       const long long last = (i + nst < n) ? i + nst : n;
       const long long drain = a.budget > (1LL << 31) ? a.budget : (1LL << 31);
       for (long long j = i; j < last; ++j)
@@ -477,6 +521,7 @@ __global__ void __launch_bounds__(NWARP * 32, 1) bf_step_kernel(StepArgs a) {
     }
     __syncwarp();
   }
+  if constexpr (PAIRS) asm volatile("cp.async.wait_all;" ::: "memory");   // no copy outlives the CTA
   if (CONES && a.selftest && blockIdx.x == 0 && warp == 0) {
     const bool ok = mbar_wait_until(&never, 0u, clock64() + a.budget);
     if (lane == 0 && !ok) *reinterpret_cast<volatile int*>(a.err) = 1;
@@ -965,6 +1010,7 @@ struct LaunchShape {
   int slack = 48;        // dataflow placement: cost units between a producer's finish and its consumer
   bool tc = false;       // mode 0: the leaf outputs on the tensor-core leaf kernel
   bool cones = false;    // mode 0: the first butterfly levels as cones in one launch
+  bool pairs = false;    // mode 0: the transfer depths fused in pairs
   size_t smem = 0;
   double tuned_ms = 0;   // the chosen candidate's time (0: not tuned)
   int candidates = 0;    // candidates the autotuner timed
@@ -981,6 +1027,8 @@ struct ChainSet {
   DepthStreams cone_streams;                               // mode 0 with cones: the cone launch
   int depth_grid_c = 0;
   std::vector<DepthStreams> depth_streams_c;               // mode 0 with cones: the other chains per depth
+  int pair_grid = 0;
+  std::vector<DepthStreams> pair_streams;                  // mode 0 with fused level pairs: one per pair
   int flow_grid = 0;
   std::map<int, DepthStreams> flow_streams;                // mode 1: all depths in one stream set, per slack
 };
@@ -1126,6 +1174,9 @@ static void free_set(ChainSet& cs) {
   for (DepthStreams& d : cs.depth_streams_c) free_streams(d);
   cs.depth_streams_c.clear();
   cs.depth_grid_c = 0;
+  for (DepthStreams& d : cs.pair_streams) free_streams(d);
+  cs.pair_streams.clear();
+  cs.pair_grid = 0;
   for (auto& kv : cs.flow_streams) free_streams(kv.second);
   cs.flow_streams.clear();
   cs.flow_grid = 0;
@@ -1270,6 +1321,113 @@ static void build_cone_streams(ChainSet& cs, int grid) {
   cs.cone_grid = grid;
 }
 
+// Mode 0 with fused level pairs: the transfer depths (all but the leaf
+// outputs) in pairs (2P, 2P + 1), one launch per pair.  A chain of depth
+// 2P + 1 reads only skeleton tiles written at depth 2P; the connected
+// components of that producer / consumer relation (a level k + 1 block reads
+// two level k blocks, which feed one other block besides: groups of two and
+// two, or two and one) each go to one warp whole (largest first to the
+// least-loaded warp), every warp running all its producer chains and then
+// all its consumer chains.  A consumer's items are flagged (flags & 16) and
+// carry in `pad` how many places back in the warp's stream the last item of
+// its component's producers lies, so the kernel knows when the copy of its
+// input (this warp's own output) may go out.  The last pair may hold one
+// depth; the leaf outputs follow in their own launch.
+static void build_pair_streams(ChainSet& cs, int grid, int ndepth) {
+  for (DepthStreams& d : cs.pair_streams) free_streams(d);
+  cs.pair_streams.clear();
+  const int ns = grid * NWARP;
+  for (int d0 = 0; d0 < ndepth; d0 += 2) {
+    const auto& P = cs.by_depth[(size_t)d0];
+    static const std::vector<std::vector<WItem>> none;
+    const auto& C = (d0 + 1 < ndepth) ? cs.by_depth[(size_t)d0 + 1] : none;
+    const size_t np = P.size(), nc = C.size(), nt = np + nc;
+    // union-find over producers [0, np) and consumers [np, np + nc)
+    std::vector<size_t> parent(nt);
+    std::iota(parent.begin(), parent.end(), 0);
+    auto find = [&](size_t x) {
+      while (parent[x] != x) x = parent[x] = parent[parent[x]];
+      return x;
+    };
+    std::map<long long, size_t> prod;   // xh tile -> producer chain
+    for (size_t c = 0; c < np; ++c) {
+      const WItem& w = P[c].back();
+      if (w.y_buf == 2)
+        for (int j = 0; j < w.ntl; ++j) prod[w.y_tile + j] = c;
+    }
+    for (size_t c = 0; c < nc; ++c)
+      for (const WItem& w : C[c]) {
+        if (w.ks == 0) continue;
+        if (w.x_buf != 2) throw Error{HB_ERR_STATE, "a paired consumer reads the input vector"};
+        for (int j = 0; j < w.ks; ++j) {
+          const auto it = prod.find(w.x_tile + j);
+          if (it == prod.end()) throw Error{HB_ERR_STATE, "a paired consumer reads a tile of another depth"};
+          const size_t a = find(np + c), b = find(it->second);
+          if (a != b) parent[a] = b;
+        }
+      }
+    std::map<size_t, std::vector<size_t>> comp;   // root -> members (producers first by index)
+    for (size_t t = 0; t < nt; ++t) comp[find(t)].push_back(t);
+    std::vector<std::pair<long long, size_t>> order;   // (cost, root)
+    for (const auto& kv : comp) {
+      long long w = 0;
+      for (size_t t : kv.second) w += chain_cost(t < np ? P[t] : C[t - np]);
+      order.push_back({w, kv.first});
+    }
+    std::stable_sort(order.begin(), order.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+    using Load = std::pair<long long, int>;
+    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> pq;
+    for (int st = 0; st < ns; ++st) pq.push({0, st});
+    std::vector<std::vector<size_t>> of_warp((size_t)ns);   // component roots
+    for (const auto& o : order) {
+      Load l = pq.top();
+      pq.pop();
+      of_warp[(size_t)l.second].push_back(o.second);
+      l.first += o.first;
+      pq.push(l);
+    }
+    std::vector<WItem> items;
+    std::vector<long long> off;
+    for (int st = 0; st < ns; ++st) {
+      off.push_back((long long)items.size());
+      const long long base = (long long)items.size();
+      std::map<size_t, long long> last_prod;   // root -> stream position of its last producer item
+      for (size_t r : of_warp[(size_t)st])
+        for (size_t t : comp[r])
+          if (t < np) {
+            items.insert(items.end(), P[t].begin(), P[t].end());
+            last_prod[r] = (long long)items.size() - 1 - base;
+          }
+      for (size_t r : of_warp[(size_t)st])
+        for (size_t t : comp[r])
+          if (t >= np) {
+            const auto lp = last_prod.find(r);
+            for (WItem w : C[t - np]) {
+              if (lp != last_prod.end()) {
+                const long long dist = (long long)items.size() - base - lp->second;
+                w.flags |= 16;
+                w.pad = (short)std::min<long long>(dist, 32767);
+              }
+              items.push_back(w);
+            }
+          }
+    }
+    off.push_back((long long)items.size());
+    DepthStreams ds;
+    ds.grid = grid;
+    ds.d_items = upload(items);
+    try {
+      ds.d_off = upload(off);
+    } catch (...) {
+      dev_free(ds.d_items);
+      throw;
+    }
+    HB_CUDA(cudaDeviceSynchronize());
+    cs.pair_streams.push_back(ds);
+  }
+  cs.pair_grid = grid;
+}
+
 // Mode 1: one stream set over all depths, placed by simulating the schedule.
 // Chain costs as above; item k of a chain starts at (chain start + the cost
 // of the chain's items before it), and must not start before every chain
@@ -1370,7 +1528,7 @@ static void build_flow_streams(ChainSet& cs, int grid, int slack, long long xh_t
 
 template <int MT>
 static void set_shape(FlowPlan* P, LaunchShape& L, int mode, int item_bytes, int pub, int slack, bool tc,
-                      bool cones = false) {
+                      bool cones = false, bool pairs = false) {
   int dev = 0, nsm = 0, optin = 0;
   HB_CUDA(cudaGetDevice(&dev));
   HB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -1378,10 +1536,12 @@ static void set_shape(FlowPlan* P, LaunchShape& L, int mode, int item_bytes, int
   if (tc && mode != 0) throw Error{HB_ERR_UNSUPPORTED, "the tensor-core leaf kernel runs with one launch per depth"};
   if (cones && mode != 0) throw Error{HB_ERR_UNSUPPORTED, "cones run with one launch per depth"};
   ChainSet& cs = chain_set(P, MT, item_bytes, tc);
+  if (cones && pairs) throw Error{HB_ERR_UNSUPPORTED, "cones and fused pairs do not combine"};
   L.tc = tc;
   L.cones = cones;
+  L.pairs = pairs;
   cudaFuncAttributes fa{};
-  const void* k = mode == 0 ? (cones ? (const void*)bf_step_kernel<MT, true> : (const void*)bf_step_kernel<MT, false>)
+  const void* k = mode == 0 ? (cones ? (const void*)bf_step_kernel<MT, 1> : (const void*)bf_step_kernel<MT, 0>)
                             : (const void*)bf_flow_kernel<MT>;
   HB_CUDA(cudaFuncGetAttributes(&fa, k));
   L.mode = mode;
@@ -1395,9 +1555,12 @@ static void set_shape(FlowPlan* P, LaunchShape& L, int mode, int item_bytes, int
   L.smem = (size_t)NWARP * L.stages * L.stage;
   // the kernel may take any size up to the opt-in limit (both directions' plans share it)
   HB_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, avail));
-  if (cones)   // the per-depth launches after the cone launch
-    HB_CUDA(cudaFuncSetAttribute((const void*)bf_step_kernel<MT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (cones || pairs) {   // the other launches of the shape
+    HB_CUDA(cudaFuncSetAttribute((const void*)bf_step_kernel<MT, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  avail));
+    HB_CUDA(cudaFuncSetAttribute((const void*)bf_step_kernel<MT, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 avail));
+  }
   int per_sm = 0;
   HB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NWARP * 32, L.smem));
   if (per_sm < 1) throw Error{HB_ERR_UNSUPPORTED, "step kernel does not fit on an SM"};
@@ -1448,9 +1611,38 @@ static void launch_shape(FlowPlan* P, const LaunchShape& L, const LaunchCtx& c,
       cfg.numAttrs = 1;
       if (first) timer(0, true);
       first = false;
-      if (cone_kernel) HB_CUDA(cudaLaunchKernelEx(&cfg, bf_step_kernel<MT, true>, args));
-      else HB_CUDA(cudaLaunchKernelEx(&cfg, bf_step_kernel<MT, false>, args));
+      if (cone_kernel) HB_CUDA(cudaLaunchKernelEx(&cfg, bf_step_kernel<MT, 1>, args));
+      else HB_CUDA(cudaLaunchKernelEx(&cfg, bf_step_kernel<MT, 0>, args));
     };
+    if (L.pairs) {
+      const int ntransfer = (int)P->terms.size() - 1;   // every depth but the leaf outputs
+      if (cs.pair_grid != L.grid) build_pair_streams(cs, L.grid, ntransfer);
+      for (const DepthStreams& ds : cs.pair_streams) {
+        StepArgs args{ds.d_items, ds.d_off, c.F, c.x, c.xh, c.u, c.pperm, c.Nv, c.R, L.stages, L.stage, c.budget,
+                      c.err, c.selftest ? 1 : 0};
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(ds.grid);
+        cfg.blockDim = dim3(NWARP * 32);
+        cfg.dynamicSmemBytes = L.smem;
+        cfg.stream = c.st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        if (first) timer(0, true);
+        first = false;
+        HB_CUDA(cudaLaunchKernelEx(&cfg, bf_step_kernel<MT, 2>, args));
+      }
+      if (L.tc) {
+        tc_leaf_launch(c.tc_plan, MT, c.F_tc, c.x_tc, c.xh, c.u, c.pperm, c.Nv, c.R, c.err, c.budget, c.st);
+      } else {
+        if (cs.depth_grid != L.grid) build_depth_streams(cs, L.grid);
+        launch(cs.depth_streams.back(), false);   // the leaf outputs
+      }
+      timer(0, false);
+      return;
+    }
     if (L.cones) {
       if (cs.cone_grid != L.grid) build_cone_streams(cs, L.grid);
       if (cs.depth_grid_c != L.grid) build_depth_streams(cs, L.grid, true);
@@ -1480,7 +1672,7 @@ static void launch_shape(FlowPlan* P, const LaunchShape& L, const LaunchCtx& c,
       cfg.numAttrs = 1;
       if (first) timer(0, true);
       first = false;
-      HB_CUDA(cudaLaunchKernelEx(&cfg, bf_step_kernel<MT, false>, args));
+      HB_CUDA(cudaLaunchKernelEx(&cfg, bf_step_kernel<MT, 0>, args));
     }
     if (L.tc) {   // the leaf outputs (the last depth) on the tensor cores
       if (first) timer(0, true);
@@ -1528,11 +1720,12 @@ static void launch_shape(FlowPlan* P, const LaunchShape& L, const LaunchCtx& c,
 template <int MT>
 static void autotune(FlowPlan* P, LaunchShape& L, const LaunchCtx& c) {
   struct Cand {
-    int mode, item_bytes, pub, slack, tc, cones;
+    int mode, item_bytes, pub, slack, tc, cones;   // cones: 1 = cone launch, 2 = fused level pairs
   };
   const Cand cands[] = {{0, 16384, 1, 0, 0, 0},  {0, 8192, 1, 0, 0, 0},   {0, 16384, 1, 0, 1, 0},
                         {0, 8192, 1, 0, 1, 0},   {0, 16384, 1, 0, 0, 1},  {0, 8192, 1, 0, 0, 1},
-                        {0, 16384, 1, 0, 1, 1},  {1, 16384, 1, 16, 0, 0}, {1, 16384, 1, 48, 0, 0},
+                        {0, 16384, 1, 0, 1, 1},  {0, 16384, 1, 0, 0, 2},  {0, 16384, 1, 0, 1, 2},
+                        {0, 8192, 1, 0, 0, 2},   {1, 16384, 1, 16, 0, 0}, {1, 16384, 1, 48, 0, 0},
                         {1, 16384, 1, 128, 0, 0}, {1, 16384, 4, 48, 0, 0}, {1, 8192, 1, 16, 0, 0},
                         {1, 8192, 1, 48, 0, 0},  {1, 8192, 1, 128, 0, 0}};
   cudaEvent_t e0, e1;
@@ -1546,7 +1739,7 @@ static void autotune(FlowPlan* P, LaunchShape& L, const LaunchCtx& c) {
     for (const Cand& k : cands) {
       LaunchShape T;
       try {
-        set_shape<MT>(P, T, k.mode, k.item_bytes, k.pub, k.slack, k.tc != 0, k.cones != 0);
+        set_shape<MT>(P, T, k.mode, k.item_bytes, k.pub, k.slack, k.tc != 0, k.cones == 1, k.cones == 2);
       } catch (const Error&) {
         continue;   // does not fit: not a candidate
       }
@@ -1614,6 +1807,7 @@ static void run_mt(FlowPlan* P, const LaunchCtx& c, int tune, const std::functio
     else if (tune == 2) set_shape<MT>(P, L, 1, ITEM_BYTES, 1, 48, false);
     else if (tune == 3) set_shape<MT>(P, L, 0, ITEM_BYTES, 1, 0, true);
     else if (tune == 4) set_shape<MT>(P, L, 0, ITEM_BYTES, 1, 0, false, true);
+    else if (tune == 5) set_shape<MT>(P, L, 0, ITEM_BYTES, 1, 0, false, false, true);
     else set_shape<MT>(P, L, 0, ITEM_BYTES, 1, 0, false);
   }
   launch_shape<MT>(P, L, c, timer);
@@ -1659,7 +1853,7 @@ static void launch_shard_mt(FlowPlan* P, const LaunchCtx& c, long long lo, long 
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    HB_CUDA(cudaLaunchKernelEx(&cfg, bf_step_kernel<MT, false>, args));
+    HB_CUDA(cudaLaunchKernelEx(&cfg, bf_step_kernel<MT, 0>, args));
   }
 }
 
@@ -1681,7 +1875,7 @@ void flow_shape(const void* plan, int MT, int* mode, int* item_bytes, int* stage
                 double* tuned_ms, int* candidates) {
   const FlowPlan* P = static_cast<const FlowPlan*>(plan);
   const LaunchShape& L = P->shape[MT];
-  *mode = !L.ready ? -1 : L.mode == 1 ? 1 : L.cones ? (L.tc ? 4 : 3) : (L.tc ? 2 : 0);
+  *mode = !L.ready ? -1 : L.mode == 1 ? 1 : L.cones ? (L.tc ? 4 : 3) : L.pairs ? (L.tc ? 6 : 5) : (L.tc ? 2 : 0);
   *item_bytes = L.item_bytes;
   *stages = L.stages;
   *pub = L.pub;
