@@ -109,8 +109,10 @@ typedef struct {
  * group, closed under the dependencies of those levels - and separates their
  * levels with bounded CTA barriers), then one launch per remaining depth.
  * 5 = the transfer depths fused in pairs (2P, 2P + 1), one launch per pair:
- * each producer / consumer component of a pair runs on one warp, the
- * consumers copying their inputs (the warp's own outputs) with cp.async. */
+ * each producer / consumer component of a pair runs on one CTA, its chains
+ * spread over the CTA's warps; a consumer waits (bounded) on a shared-memory
+ * count of its component's unfinished producer chains and copies its
+ * inputs (other warps' outputs, still in L2) with cp.async. */
 typedef struct {
   double eps;
   int leaf;

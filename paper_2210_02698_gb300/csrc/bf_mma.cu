@@ -86,6 +86,7 @@ constexpr int MAX_STAGES = HB_FLOW_MAX_STAGES;     // ring stages per warp
 #endif
 constexpr int NTW = HB_FLOW_NTW;                   // largest n-tile group (accumulators: 8 NTW MT registers)
 constexpr uint32_t IM_SIGN = 0x80000000u;          // sign bit of the imaginary (upper) bf16
+constexpr int PAIR_SLOTS = 1024;                   // fused level pairs: components per CTA and launch
 
 // One item (32 bytes): ks k-steps of one n-tile group of one term.
 struct WItem {
@@ -125,6 +126,7 @@ struct StepArgs {
   long long budget;
   int* err;
   int selftest;               // the first warp also waits on a barrier nothing completes
+  const unsigned* need = nullptr;   // fused pairs: producer chains of each component slot, PAIR_SLOTS per CTA
 };
 
 // Accumulate ks k-steps of an item into acc: NTL n-tiles whose tiles are
@@ -290,7 +292,7 @@ __device__ __forceinline__ void zero_acc(float (&acc)[NTW][MT][8]) {
 template <int MT, int VAR>
 __global__ void __launch_bounds__(NWARP * 32, 1) bf_step_kernel(StepArgs a) {
   constexpr bool CONES = VAR == 1;   // barrier records between cone levels
-  constexpr bool PAIRS = VAR == 2;   // fused level pairs: items reading this warp's own outputs (flags & 16)
+  constexpr bool PAIRS = VAR == 2;   // fused level pairs: producer / consumer components within the CTA
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t full[NWARP][MAX_STAGES];
   __shared__ __align__(16) WItem slot[NWARP][MAX_STAGES];
@@ -306,6 +308,10 @@ __global__ void __launch_bounds__(NWARP * 32, 1) bf_step_kernel(StepArgs a) {
 
   __shared__ uint64_t never;   // failure-detection self-test: nothing arrives on it
   __shared__ uint64_t cbar[2];   // cone level barriers (CONES), used alternately
+  // PAIRS: producer chains still to finish, per component slot of this CTA
+  __shared__ unsigned slot_left[PAIRS ? PAIR_SLOTS : 1];
+  if constexpr (PAIRS)
+    for (int t = threadIdx.x; t < PAIR_SLOTS; t += blockDim.x) slot_left[t] = a.need[(size_t)blockIdx.x * PAIR_SLOTS + t];
   if (lane == 0) {
     for (int s = 0; s < nst; ++s) mbar_init(&bar[s], 1);
     if (warp == 0) mbar_init(&never, 1);
@@ -315,7 +321,7 @@ __global__ void __launch_bounds__(NWARP * 32, 1) bf_step_kernel(StepArgs a) {
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if constexpr (CONES) __syncthreads();
+  if constexpr (CONES || PAIRS) __syncthreads();
   else __syncwarp();
   // barrier records issued / passed, and for each stage the barriers that
   // must be passed before its input run goes out (pending stages only)
@@ -329,12 +335,14 @@ __global__ void __launch_bounds__(NWARP * 32, 1) bf_step_kernel(StepArgs a) {
   long long gs[MAX_STAGES];
 #pragma unroll
   for (int s = 0; s < MAX_STAGES; ++s) gs[s] = -1;
-  const long long deadline = clock64() + a.budget;
+  // the budget of the waits; counted again once the previous launch is
+  // visible (a launch may start early and wait there for its predecessor)
+  long long deadline = clock64() + a.budget;
   const uint64_t pol_f = policy_evict_first(), pol_v = policy_evict_last();
   // failure-detection self-test: the first warp also waits, through the
-  // same bounded wait, on a barrier nothing completes (with cones after its
-  // stream, since the other warps of its CTA wait for it at every level)
-  if (!CONES && a.selftest && blockIdx.x == 0 && warp == 0) {
+  // same bounded wait, on a barrier nothing completes (with cones and pairs
+  // after its stream, since the other warps of its CTA may wait for it)
+  if (!CONES && !PAIRS && a.selftest && blockIdx.x == 0 && warp == 0) {
     const bool ok = mbar_wait_until(&never, 0u, deadline);
     if (lane == 0 && !ok) *reinterpret_cast<volatile int*>(a.err) = 1;
     __syncwarp();
@@ -362,9 +370,17 @@ __global__ void __launch_bounds__(NWARP * 32, 1) bf_step_kernel(StepArgs a) {
   load_win(1);
   auto f_bytes = [](const WItem& w) { return (uint32_t)w.ntl * (uint32_t)w.ks * 512u; };
   auto x_bytes = [](const WItem& w) { return (uint32_t)w.ks * (uint32_t)(MT * 1024); };
-  // PAIRS, all lanes: the input run of the item in stage s (this warp's own
-  // earlier output, in xh) copied into the stage with cp.async, one group
+  // PAIRS: a consumer item (flags & 16) reads the outputs of its component's
+  // producer chains, which may run on other warps of the CTA; pad = the
+  // component's slot.  Ready once no producer chain of the slot is left.
+  auto slot_ready = [&](int pad) {
+    const unsigned v = *reinterpret_cast<volatile unsigned*>(&slot_left[pad & (PAIR_SLOTS - 1)]);
+    return __shfl_sync(0xffffffffu, (int)(v == 0u), 0) != 0;
+  };
+  // PAIRS, all lanes: the input run of the item in stage s (written by this
+  // CTA's producers, in xh) copied into the stage with cp.async, one group
   auto own_copy = [&](int s, const WItem& w) {
+    __threadfence_block();   // acquire side of the slot count just observed
     uint4* dst = reinterpret_cast<uint4*>(ring + (size_t)s * a.stage_bytes + f_bytes(w));
     const uint4* src = a.xh + w.x_tile * (MT * 64);
     const int chunks = w.ks * MT * 64;
@@ -405,10 +421,8 @@ __global__ void __launch_bounds__(NWARP * 32, 1) bf_step_kernel(StepArgs a) {
       own = ((hi.z >> 24) & 16) != 0 && (hi.z & 0xffff) != 0;
       if (own) {
         x_now = false;
-        // the producing items are done once the item `pad` places back is
-        // computed, i.e. when it lies nst or more places back
-        const int dist = (int)((unsigned)hi.w >> 16);
-        if (with_x && dist >= nst) {
+        const int pad = (int)((unsigned)hi.w >> 16);
+        if (with_x && slot_ready(pad)) {
           const WItem& wq = *reinterpret_cast<const WItem*>(recs[warp][q & 31]);
           own_copy(s, wq);
         } else {
@@ -449,6 +463,7 @@ __global__ void __launch_bounds__(NWARP * 32, 1) bf_step_kernel(StepArgs a) {
     }
   }
   __syncwarp();
+  deadline = clock64() + a.budget;
 
   float acc[NTW][MT][8];
   zero_acc<MT>(acc);
@@ -488,9 +503,16 @@ __global__ void __launch_bounds__(NWARP * 32, 1) bf_step_kernel(StepArgs a) {
     }
     if constexpr (PAIRS) {
       if ((flags & 16) && ks > 0) {
-        if ((pend >> s) & 1u) {   // its producers are done now: copy, then wait for it
-          own_copy(s, w);
+        if ((pend >> s) & 1u) {   // wait (bounded) for its producers, copy, then wait for the copy
+          bool okp = true;
+          while (!slot_ready(w.pad))
+            if (clock64() > deadline) {
+              okp = false;
+              break;
+            }
+          own_copy(s, w);   // also after a timeout: in bounds
           pend &= ~(1u << s);
+          if (!okp) break;
         }
         cp_async_wait_pending((int)(gseq - 1 - gs[s]));
         __syncwarp();
@@ -502,6 +524,13 @@ __global__ void __launch_bounds__(NWARP * 32, 1) bf_step_kernel(StepArgs a) {
       if (w.y_buf == 1) store_natural<MT>(a, w.y_tile, ntl, lane, acc);
       else if (flags & 4) store_tiles_tc<MT>(a.xh + (size_t)w.y_tile * (MT * 64), ntl, lane, acc);
       else store_tiles<MT>(a.xh + (size_t)w.y_tile * (MT * 64), ntl, lane, acc, pol_v);
+      if constexpr (PAIRS) {
+        if (flags & 32) {   // a producer chain of the CTA's component `pad` is stored
+          __threadfence_block();
+          __syncwarp();
+          if (lane == 0) atomicSub(&slot_left[w.pad & (PAIR_SLOTS - 1)], 1u);
+        }
+      }
     }
     // every lane's reads of stage s are done before lane 0 refills it
     __syncwarp();
@@ -522,7 +551,7 @@ __global__ void __launch_bounds__(NWARP * 32, 1) bf_step_kernel(StepArgs a) {
     __syncwarp();
   }
   if constexpr (PAIRS) asm volatile("cp.async.wait_all;" ::: "memory");   // no copy outlives the CTA
-  if (CONES && a.selftest && blockIdx.x == 0 && warp == 0) {
+  if ((CONES || PAIRS) && a.selftest && blockIdx.x == 0 && warp == 0) {
     const bool ok = mbar_wait_until(&never, 0u, clock64() + a.budget);
     if (lane == 0 && !ok) *reinterpret_cast<volatile int*>(a.err) = 1;
     __syncwarp();
@@ -994,6 +1023,7 @@ struct DepthStreams {
   int grid = 0;
   WItem* d_items = nullptr;
   long long* d_off = nullptr;
+  unsigned* d_need = nullptr;   // fused pairs: producer chains per component slot (PAIR_SLOTS per CTA)
 };
 
 // The launch shape of one m-tile count: the mode (one launch per depth, or
@@ -1162,6 +1192,7 @@ static ChainSet& chain_set(FlowPlan* P, int MT, int item_bytes, bool tc, long lo
 static void free_streams(DepthStreams& d) {
   dev_free(d.d_items);
   dev_free(d.d_off);
+  dev_free(d.d_need);
   d = DepthStreams{};
 }
 
@@ -1323,15 +1354,19 @@ static void build_cone_streams(ChainSet& cs, int grid) {
 
 // Mode 0 with fused level pairs: the transfer depths (all but the leaf
 // outputs) in pairs (2P, 2P + 1), one launch per pair.  A chain of depth
-// 2P + 1 reads only skeleton tiles written at depth 2P; the connected
-// components of that producer / consumer relation (a level k + 1 block reads
-// two level k blocks, which feed one other block besides: groups of two and
-// two, or two and one) each go to one warp whole (largest first to the
-// least-loaded warp), every warp running all its producer chains and then
-// all its consumer chains.  A consumer's items are flagged (flags & 16) and
-// carry in `pad` how many places back in the warp's stream the last item of
-// its component's producers lies, so the kernel knows when the copy of its
-// input (this warp's own output) may go out.  The last pair may hold one
+// 2P + 1 reads only skeleton tiles written at depth 2P.  Each connected
+// component of that producer / consumer relation (a level k + 1 block reads
+// two level k blocks, which feed one other block besides) goes to one CTA
+// whole, largest first to the least-loaded CTA; there its chains are spread
+// over the warps, each to the least-loaded one, every warp running all its
+// producer chains before any consumer chain.  A component with consumers
+// gets a slot of its CTA: the last item of each of its producer chains is
+// flagged (flags & 32), every item of its consumers too (flags & 16), both
+// carrying the slot in `pad`, and d_need holds the slot's producer count.
+// The kernel counts a slot down in shared memory as the producers store,
+// and a consumer's input run (other warps' outputs) goes out once the count
+// is zero.  Producers wait for nothing of their own launch, and every warp
+// runs its producers first, so every wait ends.  The last pair may hold one
 // depth; the leaf outputs follow in their own launch.
 static void build_pair_streams(ChainSet& cs, int grid, int ndepth) {
   for (DepthStreams& d : cs.pair_streams) free_streams(d);
@@ -1352,6 +1387,7 @@ static void build_pair_streams(ChainSet& cs, int grid, int ndepth) {
     std::map<long long, size_t> prod;   // xh tile -> producer chain
     for (size_t c = 0; c < np; ++c) {
       const WItem& w = P[c].back();
+      if (!(w.flags & 2)) throw Error{HB_ERR_STATE, "a producer chain does not end in a store"};
       if (w.y_buf == 2)
         for (int j = 0; j < w.ntl; ++j) prod[w.y_tile + j] = c;
     }
@@ -1366,60 +1402,93 @@ static void build_pair_streams(ChainSet& cs, int grid, int ndepth) {
           if (a != b) parent[a] = b;
         }
       }
-    std::map<size_t, std::vector<size_t>> comp;   // root -> members (producers first by index)
+    std::vector<long long> cost(nt);
+    for (size_t t = 0; t < nt; ++t) cost[t] = chain_cost(t < np ? P[t] : C[t - np]);
+    std::map<size_t, std::vector<size_t>> comp;   // root -> members
     for (size_t t = 0; t < nt; ++t) comp[find(t)].push_back(t);
     std::vector<std::pair<long long, size_t>> order;   // (cost, root)
-    for (const auto& kv : comp) {
+    for (auto& kv : comp) {
       long long w = 0;
-      for (size_t t : kv.second) w += chain_cost(t < np ? P[t] : C[t - np]);
+      for (size_t t : kv.second) w += cost[t];
+      std::stable_sort(kv.second.begin(), kv.second.end(), [&](size_t x, size_t y) { return cost[x] > cost[y]; });
       order.push_back({w, kv.first});
     }
     std::stable_sort(order.begin(), order.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
     using Load = std::pair<long long, int>;
     std::priority_queue<Load, std::vector<Load>, std::greater<Load>> pq;
-    for (int st = 0; st < ns; ++st) pq.push({0, st});
-    std::vector<std::vector<size_t>> of_warp((size_t)ns);   // component roots
+    for (int b = 0; b < grid; ++b) pq.push({0, b});
+    std::vector<std::vector<size_t>> of_cta((size_t)grid);   // component roots
     for (const auto& o : order) {
       Load l = pq.top();
       pq.pop();
-      of_warp[(size_t)l.second].push_back(o.second);
+      of_cta[(size_t)l.second].push_back(o.second);
       l.first += o.first;
       pq.push(l);
+    }
+    std::vector<std::vector<WItem>> sw((size_t)ns);
+    std::vector<unsigned> need((size_t)grid * PAIR_SLOTS, 0u);
+    for (int b = 0; b < grid; ++b) {
+      long long load[NWARP] = {};
+      auto least = [&]() {
+        int m = 0;
+        for (int w = 1; w < NWARP; ++w)
+          if (load[w] < load[m]) m = w;
+        return m;
+      };
+      std::vector<std::vector<WItem>> cons((size_t)NWARP);
+      std::vector<int> slot_of(of_cta[(size_t)b].size(), -1);
+      int slots = 0;
+      for (size_t k = 0; k < of_cta[(size_t)b].size(); ++k) {
+        const auto& mem = comp[of_cta[(size_t)b][k]];
+        const bool has_cons = std::any_of(mem.begin(), mem.end(), [&](size_t t) { return t >= np; });
+        if (!has_cons) continue;
+        if (slots == PAIR_SLOTS) throw Error{HB_ERR_UNSUPPORTED, "more paired components on a CTA than slots"};
+        slot_of[k] = slots++;
+      }
+      for (size_t k = 0; k < of_cta[(size_t)b].size(); ++k)
+        for (size_t t : comp[of_cta[(size_t)b][k]]) {
+          if (t >= np) continue;
+          const int w = least();
+          auto& out = sw[(size_t)b * NWARP + w];
+          out.insert(out.end(), P[t].begin(), P[t].end());
+          if (slot_of[k] >= 0) {
+            out.back().flags |= 32;
+            out.back().pad = (short)slot_of[k];
+            ++need[(size_t)b * PAIR_SLOTS + slot_of[k]];
+          }
+          load[w] += cost[t];
+        }
+      for (size_t k = 0; k < of_cta[(size_t)b].size(); ++k)
+        for (size_t t : comp[of_cta[(size_t)b][k]]) {
+          if (t < np) continue;
+          const int w = least();
+          for (WItem it : C[t - np]) {
+            it.flags |= 16;
+            it.pad = (short)slot_of[k];
+            cons[(size_t)w].push_back(it);
+          }
+          load[w] += cost[t];
+        }
+      for (int w = 0; w < NWARP; ++w) {
+        auto& out = sw[(size_t)b * NWARP + w];
+        out.insert(out.end(), cons[(size_t)w].begin(), cons[(size_t)w].end());
+      }
     }
     std::vector<WItem> items;
     std::vector<long long> off;
     for (int st = 0; st < ns; ++st) {
       off.push_back((long long)items.size());
-      const long long base = (long long)items.size();
-      std::map<size_t, long long> last_prod;   // root -> stream position of its last producer item
-      for (size_t r : of_warp[(size_t)st])
-        for (size_t t : comp[r])
-          if (t < np) {
-            items.insert(items.end(), P[t].begin(), P[t].end());
-            last_prod[r] = (long long)items.size() - 1 - base;
-          }
-      for (size_t r : of_warp[(size_t)st])
-        for (size_t t : comp[r])
-          if (t >= np) {
-            const auto lp = last_prod.find(r);
-            for (WItem w : C[t - np]) {
-              if (lp != last_prod.end()) {
-                const long long dist = (long long)items.size() - base - lp->second;
-                w.flags |= 16;
-                w.pad = (short)std::min<long long>(dist, 32767);
-              }
-              items.push_back(w);
-            }
-          }
+      items.insert(items.end(), sw[(size_t)st].begin(), sw[(size_t)st].end());
     }
     off.push_back((long long)items.size());
     DepthStreams ds;
     ds.grid = grid;
-    ds.d_items = upload(items);
     try {
+      ds.d_items = upload(items);
       ds.d_off = upload(off);
+      ds.d_need = upload(need);
     } catch (...) {
-      dev_free(ds.d_items);
+      free_streams(ds);
       throw;
     }
     HB_CUDA(cudaDeviceSynchronize());
@@ -1549,17 +1618,24 @@ static void set_shape(FlowPlan* P, LaunchShape& L, int mode, int item_bytes, int
   L.pub = pub;
   L.slack = slack;
   L.stage = cs.stage_bytes;
-  const int avail = optin - (int)fa.sharedSizeBytes;
+  size_t stat = fa.sharedSizeBytes;
+  if (pairs) {   // the pair launches hold the component counters besides
+    cudaFuncAttributes fp{};
+    HB_CUDA(cudaFuncGetAttributes(&fp, (const void*)bf_step_kernel<MT, 2>));
+    stat = std::max(stat, fp.sharedSizeBytes);
+  }
+  const int avail = optin - (int)stat;
   L.stages = std::min(MAX_STAGES, avail / (NWARP * L.stage));
   if (L.stages < 2) throw Error{HB_ERR_UNSUPPORTED, "step kernel stages do not fit in shared memory"};
   L.smem = (size_t)NWARP * L.stages * L.stage;
   // the kernel may take any size up to the opt-in limit (both directions' plans share it)
   HB_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, avail));
-  if (cones || pairs) {   // the other launches of the shape
-    HB_CUDA(cudaFuncSetAttribute((const void*)bf_step_kernel<MT, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 avail));
-    HB_CUDA(cudaFuncSetAttribute((const void*)bf_step_kernel<MT, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 avail));
+  if (cones || pairs) {   // the other launches of the shape, each up to its own limit
+    for (const void* o : {(const void*)bf_step_kernel<MT, 0>, (const void*)bf_step_kernel<MT, 2>}) {
+      cudaFuncAttributes fo{};
+      HB_CUDA(cudaFuncGetAttributes(&fo, o));
+      HB_CUDA(cudaFuncSetAttribute(o, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fo.sharedSizeBytes));
+    }
   }
   int per_sm = 0;
   HB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NWARP * 32, L.smem));
@@ -1619,7 +1695,7 @@ static void launch_shape(FlowPlan* P, const LaunchShape& L, const LaunchCtx& c,
       if (cs.pair_grid != L.grid) build_pair_streams(cs, L.grid, ntransfer);
       for (const DepthStreams& ds : cs.pair_streams) {
         StepArgs args{ds.d_items, ds.d_off, c.F, c.x, c.xh, c.u, c.pperm, c.Nv, c.R, L.stages, L.stage, c.budget,
-                      c.err, c.selftest ? 1 : 0};
+                      c.err, c.selftest ? 1 : 0, ds.d_need};
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(ds.grid);
         cfg.blockDim = dim3(NWARP * 32);
