@@ -55,6 +55,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <cstdint>
 #include <cstring>
 #include <map>
@@ -101,6 +102,12 @@ struct WItem {
   short pad;
 };
 static_assert(sizeof(WItem) == 32, "item layout");
+// the kernels read records as two int4 (lo = bytes 0-15, hi = 16-31) and
+// take x_tile = lo.z | lo.w << 32, ks = hi.z & 0xffff, flags = hi.z >> 24,
+// x_buf = hi.w & 0xff, pad = hi.w >> 16 from them
+static_assert(offsetof(WItem, x_tile) == 8 && offsetof(WItem, ks) == 24 && offsetof(WItem, flags) == 27 &&
+                  offsetof(WItem, x_buf) == 28 && offsetof(WItem, pad) == 30,
+              "item record fields");
 
 // ------------------------------------------------------------ helpers ----
 __device__ __forceinline__ void mma16816(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
