@@ -258,7 +258,7 @@ def run_ours(args):
     build.build()
     w = W.WORKLOADS[args.workload]
     tab = load_tables(w)
-    tune = {"tuned": 1, "depth": 0, "dataflow": 2, "tc_leaf": 3, "cones": 4, "pairs": 5}[args.shape]
+    tune = {"tuned": 1, "depth": 0, "dataflow": 2, "tc_leaf": 3, "cones": 4, "pairs": 5, "grid": 6}[args.shape]
     op = binding.Operator(w.N, tab["nodes"], tab["tau2"], tab["v0"], tab["v1"], w.n_cells(), w.omega,
                           eps=w.eps, leaf=w.leaf, chi=w.chi, precision=binding.HB_MIXED_BF16X3, autotune=tune)
     t0 = time.perf_counter()
@@ -488,11 +488,13 @@ def run_ours(args):
                        5: "butterfly step kernels of one apply (the transfer depths fused in pairs, one launch "
                           "per pair, then the leaf outputs)",
                        6: "butterfly step kernels of one apply (the transfer depths fused in pairs; the leaf "
-                          "outputs on the tcgen05 tensor-core kernel)"}[shape["mode"]]
+                          "outputs on the tcgen05 tensor-core kernel)",
+                       7: "butterfly step kernel of one apply (every dependency depth in one cooperative "
+                          "launch, grid barriers between depths)"}[shape["mode"]]
         ndepth = info["levels"] + 1
         launches = passes * {1: 1, 0: 1 + ndepth, 2: 1 + ndepth,
                              3: 2 + max(0, ndepth - 4), 4: 2 + max(0, ndepth - 4),
-                             5: 2 + (ndepth - 1 + 1) // 2, 6: 2 + (ndepth - 1 + 1) // 2}[shape["mode"]]
+                             5: 2 + (ndepth - 1 + 1) // 2, 6: 2 + (ndepth - 1 + 1) // 2, 7: 2}[shape["mode"]]
         achieved = alg_bytes / (step_ms * 1e-3) / 1e9
         value = Nv * R * world / (ms * 1e-3)
         nc = cores()
@@ -607,10 +609,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(W.WORKLOADS))
     ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU oracle leg (profiling runs)")
-    ap.add_argument("--shape", default="tuned", choices=["tuned", "dataflow", "depth", "tc_leaf", "cones", "pairs"],
+    ap.add_argument("--shape", default="tuned",
+                    choices=["tuned", "dataflow", "depth", "tc_leaf", "cones", "pairs", "grid"],
                     help="launch shape of the mixed apply: autotuned (default), the persistent dataflow "
-                         "launch, one launch per dependency depth, or that with the leaf outputs on the "
-                         "tcgen05 tensor-core kernel")
+                         "launch, one launch per dependency depth, that with the leaf outputs on the "
+                         "tcgen05 tensor-core kernel, the cone launch, fused level pairs, or every depth "
+                         "in one cooperative launch with grid barriers")
     ap.add_argument("--one-core-sample", nargs=3, metavar=("WORKLOAD", "ROWS", "SEED"), help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.one_core_sample:

@@ -93,8 +93,9 @@ typedef struct {
  * mixed apply of each direction and m-tile count (16 right-hand sides per
  * m-tile) times every candidate shape on the caller's stream (one launch per
  * dependency depth at 16 KB or 8 KB items, with or without the cone launch
- * of the first butterfly levels and the tcgen05 leaf kernel; one persistent
- * launch at 16 KB or
+ * of the first butterfly levels, fused level pairs and the tcgen05 leaf
+ * kernel; every depth in one launch with grid barriers; one persistent
+ * dataflow launch at 16 KB or
  * 8 KB items, placement slack 16, 48 or 128 cost units, 1 or 4 chains per
  * flag publication; each a full apply, best of three) and keeps the fastest
  * (hb_launch_shape reports it).  That first apply then blocks the host for
@@ -112,7 +113,12 @@ typedef struct {
  * each producer / consumer component of a pair runs on one CTA, its chains
  * spread over the CTA's warps; a consumer waits (bounded) on a shared-memory
  * count of its component's unfinished producer chains and copies its
- * inputs (other warps' outputs, still in L2) with cp.async. */
+ * inputs (other warps' outputs, still in L2) with cp.async.  6 = every
+ * dependency depth in one cooperative launch (after the gather), the
+ * depths separated by bounded grid barriers: the warps of a CTA meet on a
+ * shared-memory barrier, one thread publishes the CTA's stores at gpu scope
+ * and counts the CTA in, and the next depth's input runs go out once every
+ * CTA has arrived (its factor runs are fetched before). */
 typedef struct {
   double eps;
   int leaf;
@@ -366,7 +372,8 @@ hb_status hb_fp64_fma_peak(double* tflops, void* stream);
  * inside), 2 for a gather plus one launch per depth with the leaf outputs
  * on the tcgen05 tensor-core kernel, 3 for the cone launch then one launch
  * per remaining depth, 4 for that with the tcgen05 leaf kernel, 5 for the
- * fused level pairs, 6 for those with the tcgen05 leaf kernel, -1 if no
+ * fused level pairs, 6 for those with the tcgen05 leaf kernel, 7 for every
+ * depth in one launch with grid barriers, -1 if no
  * apply has run yet at that m-tile count; *item_bytes the
  * item size the accumulation chains are cut to, *stages the shared-memory
  * ring stages per warp, *pub_batch the chains a dataflow warp publishes

@@ -156,7 +156,7 @@ hb_ctx* create_ctx(const hb_grid* grid, const hb_tables* tables, double omega, c
     throw hb::arg_error("bad options (eps > 0, leaf >= 1, chi > 0, radius >= 0)");
   if (opts->precision != HB_FP64 && opts->precision != HB_MIXED_BF16X3)
     throw hb::arg_error("unknown precision %d", opts->precision);
-  if (opts->autotune < 0 || opts->autotune > 5) throw hb::arg_error("autotune must be 0 .. 5");
+  if (opts->autotune < 0 || opts->autotune > 6) throw hb::arg_error("autotune must be 0 .. 6");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
     cudaGetLastError();

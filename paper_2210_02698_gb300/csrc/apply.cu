@@ -193,7 +193,8 @@ void ensure_scratch(hb_ctx* c, int nrhs, bool fp64) {
     c->d_mx = dev_alloc<uint4>((size_t)std::max<long long>(c->nv_tiles, 1) * 128);
     c->d_mx_tc = dev_alloc<uint4>((size_t)std::max<long long>(c->nv_tiles, 1) * 128);
     c->d_mxh = dev_alloc<uint4>((size_t)std::max<long long>(c->xh_tiles, 1) * 128);
-    const size_t nflags = (size_t)(c->nv_tiles + c->xh_tiles) + 2;
+    // + the dataflow launch's epoch and finish count, the grid barriers' arrival and finish counts
+    const size_t nflags = (size_t)(c->nv_tiles + c->xh_tiles) + 4;
     c->d_flags = dev_alloc<unsigned>(nflags);
     HB_CUDA(cudaMemset(c->d_flags, 0, sizeof(unsigned) * nflags));
     c->d_epoch = c->d_flags + (c->nv_tiles + c->xh_tiles);

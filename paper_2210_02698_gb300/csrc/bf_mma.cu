@@ -134,6 +134,7 @@ struct StepArgs {
   int* err;
   int selftest;               // the first warp also waits on a barrier nothing completes
   const unsigned* need = nullptr;   // fused pairs: producer chains of each component slot, PAIR_SLOTS per CTA
+  unsigned* gsync = nullptr;        // grid barriers: [0] arrivals, [1] CTAs finished (both 0 between launches)
 };
 
 // Accumulate ks k-steps of an item into acc: NTL n-tiles whose tiles are
@@ -289,6 +290,12 @@ __device__ __forceinline__ void zero_acc(float (&acc)[NTW][MT][8]) {
       for (int e = 0; e < 8; ++e) acc[j][mt][e] = 0.f;
 }
 
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
 // ------------------------------------------------------------- kernel ----
 // CONES: the launch runs cones of butterfly levels (a CTA takes whole cones;
 // within a cone the level of every warp's items is separated by a barrier
@@ -300,6 +307,8 @@ template <int MT, int VAR>
 __global__ void __launch_bounds__(NWARP * 32, 1) bf_step_kernel(StepArgs a) {
   constexpr bool CONES = VAR == 1;   // barrier records between cone levels
   constexpr bool PAIRS = VAR == 2;   // fused level pairs: producer / consumer components within the CTA
+  constexpr bool GRID = VAR == 3;    // every depth in one cooperative launch, grid barriers between depths
+  constexpr bool BARS = CONES || GRID;   // barrier records in the streams
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t full[NWARP][MAX_STAGES];
   __shared__ __align__(16) WItem slot[NWARP][MAX_STAGES];
@@ -314,7 +323,8 @@ __global__ void __launch_bounds__(NWARP * 32, 1) bf_step_kernel(StepArgs a) {
   WItem* sl = slot[warp];
 
   __shared__ uint64_t never;   // failure-detection self-test: nothing arrives on it
-  __shared__ uint64_t cbar[2];   // cone level barriers (CONES), used alternately
+  __shared__ uint64_t cbar[2];   // level barriers of the CTA's warps (CONES, GRID), used alternately
+  __shared__ uint64_t gbar[2];   // GRID: the grid barrier passed (warp 0 arrives), used alternately
   // PAIRS: producer chains still to finish, per component slot of this CTA
   __shared__ unsigned slot_left[PAIRS ? PAIR_SLOTS : 1];
   if constexpr (PAIRS)
@@ -322,13 +332,15 @@ __global__ void __launch_bounds__(NWARP * 32, 1) bf_step_kernel(StepArgs a) {
   if (lane == 0) {
     for (int s = 0; s < nst; ++s) mbar_init(&bar[s], 1);
     if (warp == 0) mbar_init(&never, 1);
-    if (CONES && warp == 0) {
+    if (BARS && warp == 0) {
       mbar_init(&cbar[0], NWARP);
       mbar_init(&cbar[1], NWARP);
+      mbar_init(&gbar[0], 1);
+      mbar_init(&gbar[1], 1);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if constexpr (CONES || PAIRS) __syncthreads();
+  if constexpr (BARS || PAIRS) __syncthreads();
   else __syncwarp();
   // barrier records issued / passed, and for each stage the barriers that
   // must be passed before its input run goes out (pending stages only)
@@ -349,7 +361,7 @@ __global__ void __launch_bounds__(NWARP * 32, 1) bf_step_kernel(StepArgs a) {
   // failure-detection self-test: the first warp also waits, through the
   // same bounded wait, on a barrier nothing completes (with cones and pairs
   // after its stream, since the other warps of its CTA may wait for it)
-  if (!CONES && !PAIRS && a.selftest && blockIdx.x == 0 && warp == 0) {
+  if (!BARS && !PAIRS && a.selftest && blockIdx.x == 0 && warp == 0) {
     const bool ok = mbar_wait_until(&never, 0u, deadline);
     if (lane == 0 && !ok) *reinterpret_cast<volatile int*>(a.err) = 1;
     __syncwarp();
@@ -408,7 +420,7 @@ __global__ void __launch_bounds__(NWARP * 32, 1) bf_step_kernel(StepArgs a) {
       if (q >= 32) load_win((q >> 5) + 1);
     }
     bool x_now = with_x;
-    if constexpr (CONES) {
+    if constexpr (BARS) {
       // every lane tracks the barrier records (warp-uniform)
       const int4 hi = recs[warp][q & 31][1];
       if ((hi.z >> 24) & 8) {
@@ -482,15 +494,38 @@ __global__ void __launch_bounds__(NWARP * 32, 1) bf_step_kernel(StepArgs a) {
     const WItem& w = sl[s];
     const int flags = w.flags, ntl = w.ntl, ks = w.ks;
     const uint4* st = reinterpret_cast<const uint4*>(ring + (size_t)s * a.stage_bytes);
-    if constexpr (CONES) {
+    if constexpr (BARS) {
       if (flags & 8) {
         // the warp's stores of this level reach the async proxy, then every
         // warp of the CTA has finished the level
         asm volatile("fence.proxy.async.global;" ::: "memory");
         __syncwarp();
         uint64_t* cb = &cbar[bar_passed & 1];
+        const uint32_t par = (uint32_t)((bar_passed >> 1) & 1);
         if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(cb)) : "memory");
-        const bool okb = mbar_wait_until(cb, (uint32_t)((bar_passed >> 1) & 1), deadline);
+        bool okb = true;
+        if (!GRID || warp == 0) okb = mbar_wait_until(cb, par, deadline);
+        if constexpr (GRID) {
+          // warp 0 publishes the CTA's level at gpu scope (the CTA barrier
+          // made the other warps' stores visible to it), counts the CTA in
+          // and waits (bounded) for every CTA; then it releases the CTA's
+          // warps, which fetch the next level's inputs
+          uint64_t* gb = &gbar[bar_passed & 1];
+          if (warp == 0) {
+            int okg = __all_sync(0xffffffffu, okb) ? 1 : 0;
+            if (lane == 0) {
+              __threadfence();
+              atomicAdd(a.gsync, 1u);
+              const unsigned target = (unsigned)(bar_passed + 1) * gridDim.x;
+              while (okg && ld_acquire_gpu(a.gsync) < target)
+                if (clock64() > deadline) okg = 0;
+              asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(gb)) : "memory");
+            }
+            okb = __shfl_sync(0xffffffffu, okg, 0) != 0;
+          }
+          okb = mbar_wait_until(gb, par, deadline) && okb;
+          if (lane == 0) asm volatile("fence.proxy.async.global;" ::: "memory");
+        }
         ++bar_passed;
         // deferred input runs now allowed (issued even after a timeout: in bounds)
         unsigned go = 0;
@@ -558,10 +593,23 @@ __global__ void __launch_bounds__(NWARP * 32, 1) bf_step_kernel(StepArgs a) {
     __syncwarp();
   }
   if constexpr (PAIRS) asm volatile("cp.async.wait_all;" ::: "memory");   // no copy outlives the CTA
-  if ((CONES || PAIRS) && a.selftest && blockIdx.x == 0 && warp == 0) {
+  if ((BARS || PAIRS) && a.selftest && blockIdx.x == 0 && warp == 0) {
     const bool ok = mbar_wait_until(&never, 0u, clock64() + a.budget);
     if (lane == 0 && !ok) *reinterpret_cast<volatile int*>(a.err) = 1;
     __syncwarp();
+  }
+  if constexpr (GRID) {
+    // the last CTA to finish resets the barrier counters for the next
+    // launch (every CTA has passed, or given up on, all its barriers)
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      if (atomicAdd(a.gsync + 1, 1u) == gridDim.x - 1) {
+        atomicExch(a.gsync, 0u);
+        atomicExch(a.gsync + 1, 0u);
+        __threadfence();
+      }
+    }
   }
   if (lane == 0) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
@@ -1048,6 +1096,7 @@ struct LaunchShape {
   bool tc = false;       // mode 0: the leaf outputs on the tensor-core leaf kernel
   bool cones = false;    // mode 0: the first butterfly levels as cones in one launch
   bool pairs = false;    // mode 0: the transfer depths fused in pairs
+  bool gridb = false;    // mode 0: every depth in one cooperative launch with grid barriers
   size_t smem = 0;
   double tuned_ms = 0;   // the chosen candidate's time (0: not tuned)
   int candidates = 0;    // candidates the autotuner timed
@@ -1066,6 +1115,8 @@ struct ChainSet {
   std::vector<DepthStreams> depth_streams_c;               // mode 0 with cones: the other chains per depth
   int pair_grid = 0;
   std::vector<DepthStreams> pair_streams;                  // mode 0 with fused level pairs: one per pair
+  int gridb_grid = 0;
+  DepthStreams gridb_streams;                              // mode 0 with grid barriers: all depths
   int flow_grid = 0;
   std::map<int, DepthStreams> flow_streams;                // mode 1: all depths in one stream set, per slack
 };
@@ -1215,6 +1266,8 @@ static void free_set(ChainSet& cs) {
   for (DepthStreams& d : cs.pair_streams) free_streams(d);
   cs.pair_streams.clear();
   cs.pair_grid = 0;
+  free_streams(cs.gridb_streams);
+  cs.gridb_grid = 0;
   for (auto& kv : cs.flow_streams) free_streams(kv.second);
   cs.flow_streams.clear();
   cs.flow_grid = 0;
@@ -1357,6 +1410,50 @@ static void build_cone_streams(ChainSet& cs, int grid) {
     }
   cs.cone_streams = upload_streams(per, grid);
   cs.cone_grid = grid;
+}
+
+// Mode 0 with grid barriers: every depth in one cooperative launch.  Each
+// depth's chains are dealt to the grid x NWARP warps as in the per-depth
+// launches (largest first to the least-loaded warp), and every warp gets a
+// barrier record between consecutive non-empty depths, so all warps hold the
+// same barriers in the same order; at a barrier the CTA's warps meet, one
+// warp counts the CTA in at gpu scope and waits for the whole grid.
+static void build_gridb_streams(ChainSet& cs, int grid) {
+  free_streams(cs.gridb_streams);
+  static const std::vector<WItem> barrier_rec = [] {
+    WItem w{};
+    w.flags = 8;
+    return std::vector<WItem>{w};
+  }();
+  const int ns = grid * NWARP;
+  std::vector<std::vector<const std::vector<WItem>*>> per((size_t)ns);
+  bool any = false;
+  for (size_t dd = 0; dd < cs.by_depth.size(); ++dd) {
+    const auto& chains = cs.by_depth[dd];
+    if (chains.empty()) continue;
+    if (any)
+      for (auto& p : per) p.push_back(&barrier_rec);
+    any = true;
+    std::vector<long long> cost(chains.size());
+    std::vector<size_t> order(chains.size());
+    for (size_t c = 0; c < chains.size(); ++c) {
+      cost[c] = chain_cost(chains[c]);
+      order[c] = c;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
+    using Load = std::pair<long long, int>;
+    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> pq;
+    for (int st = 0; st < ns; ++st) pq.push({0, st});
+    for (size_t c : order) {
+      Load l = pq.top();
+      pq.pop();
+      per[(size_t)l.second].push_back(&chains[c]);
+      l.first += cost[c];
+      pq.push(l);
+    }
+  }
+  cs.gridb_streams = upload_streams(per, grid);
+  cs.gridb_grid = grid;
 }
 
 // Mode 0 with fused level pairs: the transfer depths (all but the leaf
@@ -1604,7 +1701,7 @@ static void build_flow_streams(ChainSet& cs, int grid, int slack, long long xh_t
 
 template <int MT>
 static void set_shape(FlowPlan* P, LaunchShape& L, int mode, int item_bytes, int pub, int slack, bool tc,
-                      bool cones = false, bool pairs = false) {
+                      bool cones = false, bool pairs = false, bool gridb = false) {
   int dev = 0, nsm = 0, optin = 0;
   HB_CUDA(cudaGetDevice(&dev));
   HB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -1613,11 +1710,16 @@ static void set_shape(FlowPlan* P, LaunchShape& L, int mode, int item_bytes, int
   if (cones && mode != 0) throw Error{HB_ERR_UNSUPPORTED, "cones run with one launch per depth"};
   ChainSet& cs = chain_set(P, MT, item_bytes, tc);
   if (cones && pairs) throw Error{HB_ERR_UNSUPPORTED, "cones and fused pairs do not combine"};
+  if (gridb && (mode != 0 || tc || cones || pairs))
+    throw Error{HB_ERR_UNSUPPORTED, "grid barriers run every depth on the step kernel alone"};
   L.tc = tc;
   L.cones = cones;
   L.pairs = pairs;
+  L.gridb = gridb;
   cudaFuncAttributes fa{};
-  const void* k = mode == 0 ? (cones ? (const void*)bf_step_kernel<MT, 1> : (const void*)bf_step_kernel<MT, 0>)
+  const void* k = mode == 0 ? (cones   ? (const void*)bf_step_kernel<MT, 1>
+                              : gridb ? (const void*)bf_step_kernel<MT, 3>
+                                      : (const void*)bf_step_kernel<MT, 0>)
                             : (const void*)bf_flow_kernel<MT>;
   HB_CUDA(cudaFuncGetAttributes(&fa, k));
   L.mode = mode;
@@ -1697,6 +1799,27 @@ static void launch_shape(FlowPlan* P, const LaunchShape& L, const LaunchCtx& c,
       if (cone_kernel) HB_CUDA(cudaLaunchKernelEx(&cfg, bf_step_kernel<MT, 1>, args));
       else HB_CUDA(cudaLaunchKernelEx(&cfg, bf_step_kernel<MT, 0>, args));
     };
+    if (L.gridb) {
+      // one cooperative launch (every CTA resident: the grid barriers)
+      if (cs.gridb_grid != L.grid) build_gridb_streams(cs, L.grid);
+      const DepthStreams& ds = cs.gridb_streams;
+      StepArgs args{ds.d_items, ds.d_off, c.F, c.x, c.xh, c.u, c.pperm, c.Nv, c.R, L.stages, L.stage, c.budget,
+                    c.err, c.selftest ? 1 : 0, nullptr, c.epoch + 2};
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(ds.grid);
+      cfg.blockDim = dim3(NWARP * 32);
+      cfg.dynamicSmemBytes = L.smem;
+      cfg.stream = c.st;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeCooperative;
+      attr[0].val.cooperative = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      timer(0, true);
+      HB_CUDA(cudaLaunchKernelEx(&cfg, bf_step_kernel<MT, 3>, args));
+      timer(0, false);
+      return;
+    }
     if (L.pairs) {
       const int ntransfer = (int)P->terms.size() - 1;   // every depth but the leaf outputs
       if (cs.pair_grid != L.grid) build_pair_streams(cs, L.grid, ntransfer);
@@ -1798,19 +1921,23 @@ static void launch_shape(FlowPlan* P, const LaunchShape& L, const LaunchCtx& c,
 // The autotuner: time every candidate shape (each a full apply of these
 // right-hand sides, one untimed run then the best of three, CUDA events on
 // the caller's stream) and keep the fastest.  Candidates: one launch per
-// depth at 16 KB and 8 KB items; the dataflow launch at 16 KB and 8 KB items
-// with 1 and 4 chains per publication.  Only the winner's streams are kept.
+// depth, the cone launch, fused level pairs and grid barriers, each at 16 KB
+// and 8 KB items and (but grid barriers) with the tensor-core leaf kernel;
+// the dataflow launch at 16 KB and 8 KB items with 1 and 4 chains per
+// publication and three placement slacks.  Only the winner's streams are
+// kept.
 template <int MT>
 static void autotune(FlowPlan* P, LaunchShape& L, const LaunchCtx& c) {
   struct Cand {
-    int mode, item_bytes, pub, slack, tc, cones;   // cones: 1 = cone launch, 2 = fused level pairs
+    int mode, item_bytes, pub, slack, tc, cones;   // cones: 1 = cone launch, 2 = fused level pairs, 3 = grid barriers
   };
   const Cand cands[] = {{0, 16384, 1, 0, 0, 0},  {0, 8192, 1, 0, 0, 0},   {0, 16384, 1, 0, 1, 0},
                         {0, 8192, 1, 0, 1, 0},   {0, 16384, 1, 0, 0, 1},  {0, 8192, 1, 0, 0, 1},
                         {0, 16384, 1, 0, 1, 1},  {0, 16384, 1, 0, 0, 2},  {0, 16384, 1, 0, 1, 2},
                         {0, 8192, 1, 0, 0, 2},   {1, 16384, 1, 16, 0, 0}, {1, 16384, 1, 48, 0, 0},
                         {1, 16384, 1, 128, 0, 0}, {1, 16384, 4, 48, 0, 0}, {1, 8192, 1, 16, 0, 0},
-                        {1, 8192, 1, 48, 0, 0},  {1, 8192, 1, 128, 0, 0}};
+                        {1, 8192, 1, 48, 0, 0},  {1, 8192, 1, 128, 0, 0}, {0, 16384, 1, 0, 0, 3},
+                        {0, 8192, 1, 0, 0, 3}};
   cudaEvent_t e0, e1;
   HB_CUDA(cudaEventCreate(&e0));
   HB_CUDA(cudaEventCreate(&e1));
@@ -1822,7 +1949,8 @@ static void autotune(FlowPlan* P, LaunchShape& L, const LaunchCtx& c) {
     for (const Cand& k : cands) {
       LaunchShape T;
       try {
-        set_shape<MT>(P, T, k.mode, k.item_bytes, k.pub, k.slack, k.tc != 0, k.cones == 1, k.cones == 2);
+        set_shape<MT>(P, T, k.mode, k.item_bytes, k.pub, k.slack, k.tc != 0, k.cones == 1, k.cones == 2,
+                      k.cones == 3);
       } catch (const Error&) {
         continue;   // does not fit: not a candidate
       }
@@ -1891,6 +2019,7 @@ static void run_mt(FlowPlan* P, const LaunchCtx& c, int tune, const std::functio
     else if (tune == 3) set_shape<MT>(P, L, 0, ITEM_BYTES, 1, 0, true);
     else if (tune == 4) set_shape<MT>(P, L, 0, ITEM_BYTES, 1, 0, false, true);
     else if (tune == 5) set_shape<MT>(P, L, 0, ITEM_BYTES, 1, 0, false, false, true);
+    else if (tune == 6) set_shape<MT>(P, L, 0, ITEM_BYTES, 1, 0, false, false, false, true);
     else set_shape<MT>(P, L, 0, ITEM_BYTES, 1, 0, false);
   }
   launch_shape<MT>(P, L, c, timer);
@@ -1958,7 +2087,12 @@ void flow_shape(const void* plan, int MT, int* mode, int* item_bytes, int* stage
                 double* tuned_ms, int* candidates) {
   const FlowPlan* P = static_cast<const FlowPlan*>(plan);
   const LaunchShape& L = P->shape[MT];
-  *mode = !L.ready ? -1 : L.mode == 1 ? 1 : L.cones ? (L.tc ? 4 : 3) : L.pairs ? (L.tc ? 6 : 5) : (L.tc ? 2 : 0);
+  *mode = !L.ready ? -1
+          : L.mode == 1 ? 1
+          : L.gridb     ? 7
+          : L.cones     ? (L.tc ? 4 : 3)
+          : L.pairs     ? (L.tc ? 6 : 5)
+                        : (L.tc ? 2 : 0);
   *item_bytes = L.item_bytes;
   *stages = L.stages;
   *pub = L.pub;

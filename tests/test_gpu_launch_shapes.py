@@ -4,7 +4,8 @@ A chain (one n-tile group of one task) accumulates its items in the same
 order in every shape; only where and when chains run changes.  So the gather
 plus one launch per dependency depth (the default), the persistent dataflow
 launch, the cone launch of the first butterfly levels, the transfer depths
-fused in pairs, and whatever shape
+fused in pairs, every depth in one cooperative launch with grid barriers,
+and whatever shape
 the autotuner picks all give bitwise equal outputs (the tensor-core leaf
 shapes equal one another), in both directions and at one and two m-tiles (16 and 32
 right-hand sides per pass)."""
@@ -33,7 +34,7 @@ def test_shapes_are_bitwise_equal(N, leaf, nrhs):
     w = W.small_workload(W.GRADIENT, N, N / 8, nrhs, leaf=leaf)
     s_dev = to_dev(W.complex_normal_sources(w.grid.Nv, nrhs, 77))
     outs, shapes = {}, {}
-    for tune in (0, 2, 3, 4, 5, 1):
+    for tune in (0, 2, 3, 4, 5, 6, 1):
         op = gpu_op(w, precision=binding.HB_MIXED_BF16X3, autotune=tune)
         op.build()
         u = torch.full_like(s_dev, float("nan"))
@@ -52,8 +53,9 @@ def test_shapes_are_bitwise_equal(N, leaf, nrhs):
     # the cone launch and the fused level pairs run the same chains too
     assert np.array_equal(outs[4][0], outs[0][0]) and np.array_equal(outs[4][1], outs[0][1])
     assert np.array_equal(outs[5][0], outs[0][0]) and np.array_equal(outs[5][1], outs[0][1])
+    assert np.array_equal(outs[6][0], outs[0][0]) and np.array_equal(outs[6][1], outs[0][1])
     for d in (0, 1):
-        ref = {0: outs[0][d], 1: outs[0][d], 3: outs[0][d], 5: outs[0][d],
+        ref = {0: outs[0][d], 1: outs[0][d], 3: outs[0][d], 5: outs[0][d], 7: outs[0][d],
                2: outs[3][d], 4: outs[3][d], 6: outs[3][d]}[shapes[1][d]["mode"]]
         assert np.array_equal(outs[1][d], ref), d
     assert np.all(np.isfinite(outs[0][0])) and np.all(np.isfinite(outs[0][1]))
@@ -62,8 +64,9 @@ def test_shapes_are_bitwise_equal(N, leaf, nrhs):
     assert shapes[3][0]["mode"] == 2 and shapes[3][1]["mode"] == 2
     assert shapes[4][0]["mode"] == 3 and shapes[4][1]["mode"] == 3
     assert shapes[5][0]["mode"] == 5 and shapes[5][1]["mode"] == 5
+    assert shapes[6][0]["mode"] == 7 and shapes[6][1]["mode"] == 7
     for sh in shapes[1]:
-        assert sh["mode"] in (0, 1, 2, 3, 4, 5, 6) and sh["candidates"] >= 4 and sh["tuned_ms"] > 0
+        assert sh["mode"] in (0, 1, 2, 3, 4, 5, 6, 7) and sh["candidates"] >= 4 and sh["tuned_ms"] > 0
 
 
 def test_dataflow_replays_and_alternating_directions():

@@ -12,7 +12,7 @@ from tests._common import gpu_op, oracle_op, rel_l2, to_dev, from_dev
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("shape", [0, 2, 4, 5])   # per depth; dataflow; cones; fused level pairs
+@pytest.mark.parametrize("shape", [0, 2, 4, 5, 6])   # per depth; dataflow; cones; fused level pairs; grid barriers
 def test_wait_that_runs_out_is_reported_and_context_survives(shape):
     import torch
     from paper_2210_02698_gb300 import binding
