@@ -128,10 +128,11 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload):
-    """DRAM bytes (read + write) of the step kernels of one apply from the
-    committed ncu summary, if it was taken on the current kernel sources and
-    on this workload (None otherwise)."""
+def profiled_traffic(workload, mode):
+    """DRAM bytes (read + write) of the step kernels of one apply in launch
+    shape `mode` (hb_launch_shape's) from the committed ncu summary, if it
+    was taken on the current kernel sources, on this workload and in that
+    shape (None otherwise)."""
     if workload != PROFILE_WORKLOAD:
         return None
     try:
@@ -147,7 +148,7 @@ def profiled_traffic(workload):
     if vals.get("kernel sources sha256 prefix") != kernel_source_hash():
         return None
     try:
-        return float(vals["step-kernel DRAM bytes per apply"])
+        return float(vals[f"step-kernel DRAM bytes per apply (mode {mode})"])
     except (KeyError, ValueError):
         return None
 
@@ -557,7 +558,7 @@ def run_ours(args):
                                     "tensor-core products per complex MAC, FP32 accumulate, FP64 output",
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": profiled_traffic(args.workload),
+                         "frac": achieved / hbm, "traffic": profiled_traffic(args.workload, shape["mode"]),
                          "kernel": kernel_what,
                          "alg_bytes": alg_bytes, "kernel_ms": step_ms,
                          "peak_kind": f"{peak_kind} copy bandwidth"},
