@@ -169,6 +169,18 @@ hb_status hb_create(const hb_grid* grid, const hb_tables* tables, double omega,
  * Synchronous.  Errors: HB_ERR_OOM, HB_ERR_CUDA, HB_ERR_STATE if built. */
 hb_status hb_build(hb_handle h);
 
+/* hb_set_omega: move the handle to another angular frequency omega > 0
+ * (Sec. 4.1: tau^2, v0 and v1 - the tables - do not depend on omega, so one
+ * table set serves every frequency).  Keeps the uploaded tables, their
+ * interpolation data, the cluster tree and the options; recomputes the
+ * omega-dependent self terms; frees the factors, plans and apply scratch of
+ * a previous hb_build (the handle is then unbuilt: call hb_build again
+ * before hb_apply) and assembles a curve set with hb_curve_set again at the
+ * new frequency.  The result equals a handle created at omega with the same
+ * tables.  Synchronous.  Errors: HB_ERR_ARG (null handle, omega <= 0 or not
+ * finite), HB_ERR_OOM, HB_ERR_CUDA. */
+hb_status hb_set_omega(hb_handle h, double omega);
+
 /* hb_apply: u = K (h^2 s) with the compressed operator (Eq. butterfly_mat
  * summed over the HODBF, plus the dense leaf blocks), in the precision of
  * opts.precision (see hb_set_precision).  s, u: device, complex128,

@@ -21,7 +21,7 @@ STATUS = {0: "HB_OK", 1: "HB_ERR_ARG", 2: "HB_ERR_CUDA", 3: "HB_ERR_OOM", 4: "HB
           5: "HB_ERR_STATE", 6: "HB_ERR_UNSUPPORTED"}
 
 # every symbol include/hb.h declares
-EXPORTS = ["hb_create", "hb_build", "hb_save", "hb_load", "hb_apply", "hb_apply_adjoint", "hb_set_precision",
+EXPORTS = ["hb_create", "hb_build", "hb_set_omega", "hb_save", "hb_load", "hb_apply", "hb_apply_adjoint", "hb_set_precision",
            "hb_set_wait_selftest", "hb_device_alloc_cap",
            "hb_apply_dense", "hb_apply_dense_adjoint", "hb_entries", "hb_curve_set", "hb_curve_operators",
            "hb_apply_inclusion", "hb_id_batch", "hb_id_batch_noalloc",
@@ -69,6 +69,7 @@ def lib():
         vp, i, d, ll = C.c_void_p, C.c_int, C.c_double, C.c_longlong
         L.hb_create.argtypes = [C.POINTER(Grid), C.POINTER(Tables), d, C.POINTER(Options), C.POINTER(vp)]
         L.hb_build.argtypes = [vp]
+        L.hb_set_omega.argtypes = [vp, d]
         for f in ("hb_apply", "hb_apply_adjoint", "hb_apply_dense", "hb_apply_dense_adjoint"):
             getattr(L, f).argtypes = [vp, vp, vp, i, vp]
         L.hb_set_precision.argtypes = [vp, i]
@@ -213,6 +214,11 @@ class Operator:
 
     def build(self):
         self._call("hb_build")
+
+    def set_omega(self, omega):
+        """hb_set_omega: the same tables and cluster tree at another frequency;
+        the handle is unbuilt afterwards (call build())."""
+        self._call("hb_set_omega", float(omega))
 
     def set_precision(self, p):
         self._call("hb_set_precision", int(p))

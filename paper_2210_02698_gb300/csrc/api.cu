@@ -127,6 +127,50 @@ void free_all(hb_ctx* c) {
   if (c->h_err) cudaFreeHost(c->h_err);
 }
 
+// Everything hb_build made - factors, apply plans, recorded ID blocks, row
+// shards and the apply scratch sized by the ranks - freed, so that the
+// handle can be built again; the tables, the cluster tree, the options and
+// the error word stay.
+void release_build(hb_ctx* c) {
+  HB_CUDA(cudaDeviceSynchronize());
+  for (void* p : {(void*)c->d_f64, (void*)c->d_nat[0], (void*)c->d_nat[1], (void*)c->d_tc[0], (void*)c->d_tc[1],
+                  (void*)c->d_pperm, (void*)c->d_mx, (void*)c->d_mxh, (void*)c->d_mx_tc, (void*)c->d_flags,
+                  c->d_x, c->d_y, c->d_xh, (void*)c->d_tasks[0], (void*)c->d_tasks[1]})
+    hb::dev_free(p);
+  c->d_f64 = nullptr;
+  c->d_nat[0] = c->d_nat[1] = c->d_tc[0] = c->d_tc[1] = nullptr;
+  c->d_pperm = nullptr;
+  c->d_mx = c->d_mxh = c->d_mx_tc = nullptr;
+  c->d_flags = c->d_epoch = nullptr;
+  c->d_x = c->d_y = c->d_xh = nullptr;
+  c->cap_rhs = 0;
+  c->d_tasks[0] = c->d_tasks[1] = nullptr;
+  for (int d = 0; d < 2; ++d) {
+    hb::flow_plan_free(c->flow_plan[d]);
+    c->flow_plan[d] = nullptr;
+    hb::tc_plan_free(c->tc_plan[d]);
+    c->tc_plan[d] = nullptr;
+    c->step_begin[d].clear();
+    c->tasks_h[d].clear();
+    c->task_rows[d].clear();
+    c->nat_tiles[d] = 0;
+  }
+  hb::shard_cache_free(c);
+  c->bidx.clear();
+  c->leaf_off.clear();
+  c->leaf_tile.clear();
+  c->id_recs.clear();
+  c->n_factor = 0;
+  c->nv_tiles = c->xh_tiles = c->xh_rows = 0;
+  c->max_rank = 0;
+  const long long nv = c->stats.n_v;
+  const int lv = c->stats.levels;
+  c->stats = hb_stats{};
+  c->stats.n_v = nv;
+  c->stats.levels = lv;
+  c->built = false;
+}
+
 void check_vec_args(hb_ctx* c, const void* a, const void* b, int nrhs) {
   if (!c) throw hb::arg_error("null handle");
   if (!a || !b) throw hb::arg_error("null vector pointer");
@@ -257,6 +301,33 @@ hb_status hb_build(hb_handle h) {
       throw;
     }
     h->built = true;
+  });
+}
+
+hb_status hb_set_omega(hb_handle h, double omega) {
+  return guarded(h, [&] {
+    if (!h) throw hb::arg_error("null handle");
+    if (!(omega > 0) || !std::isfinite(omega)) throw hb::arg_error("omega must be positive");
+    // the curve, if any, is assembled again at the new frequency
+    std::vector<double> cen, len, nseg;
+    const long long ns = h->ns;
+    if (ns > 0) {
+      std::vector<double2> c2((size_t)ns);
+      len.resize((size_t)ns);
+      nseg.resize((size_t)ns);
+      HB_CUDA(cudaMemcpy(c2.data(), h->d_seg, sizeof(double2) * ns, cudaMemcpyDeviceToHost));
+      HB_CUDA(cudaMemcpy(len.data(), h->d_segw, sizeof(double) * ns, cudaMemcpyDeviceToHost));
+      HB_CUDA(cudaMemcpy(nseg.data(), h->d_segn, sizeof(double) * ns, cudaMemcpyDeviceToHost));
+      for (const double2& v : c2) {
+        cen.push_back(v.x);
+        cen.push_back(v.y);
+      }
+    }
+    release_build(h);
+    hb::curve_free(h);
+    h->omega = omega;
+    hb::compute_self(h);
+    if (ns > 0) hb::curve_set(h, cen.data(), len.data(), nseg.data(), ns);
   });
 }
 

@@ -155,7 +155,14 @@ void setup_tables(hb_ctx* c) {
     HB_CHECK_LAUNCH();
   }
   c->d_ncell = upload(c->n_cells);
-  c->d_self = dev_alloc<double2>(c->Nv);
+  compute_self(c);
+}
+
+// The cell-integrated self terms at the handle's omega (the only
+// precomputed entry data that depends on it; the tables do not), into
+// d_self (allocated on first use).
+void compute_self(hb_ctx* c) {
+  if (!c->d_self) c->d_self = dev_alloc<double2>(c->Nv);
   std::vector<double> glx, glw;
   gauss_legendre(64, glx, glw);
   // the quadrature rule is scratch: freed on the way out, also when a step throws

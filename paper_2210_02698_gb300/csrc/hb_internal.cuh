@@ -332,6 +332,7 @@ struct hb_ctx {
 namespace hb {
 hb::EntryParams entry_params(const hb_ctx* c, int transposed);
 void setup_tables(hb_ctx* c);                 // entries.cu
+void compute_self(hb_ctx* c);                 // entries.cu
 void dense_apply(hb_ctx* c, const double2* s, double2* u, int nrhs, int adjoint, cudaStream_t st);
 void eval_entries(hb_ctx* c, const long long* rows, int m, const long long* cols, int n,
                   double2* out, cudaStream_t st);
