@@ -210,7 +210,8 @@ def build_tables(medium, n_I, h0=1.0 / 256, margin=0.3, max_iter=400, tol=1e-12,
     NI = n_I * n_I
     px = np.ascontiguousarray(np.tile(xn, n_I))
     pz = np.ascontiguousarray(np.repeat(xn, n_I))
-    src = np.arange(NI, dtype=np.int32) if sources is None else np.asarray(sources, dtype=np.int32)
+    # contiguous: the C builder reads the indices as one array
+    src = np.arange(NI, dtype=np.int32) if sources is None else np.ascontiguousarray(sources, dtype=np.int32)
     ns = len(src)
     M, lo, w0, w1, roi0, roi1 = mesh(h0, margin)
     n, _, _ = mesh_n(medium, M, lo, h0)
