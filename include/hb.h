@@ -328,6 +328,46 @@ hb_status hb_curve_operators(hb_handle h, void* k_s2s, void* k_v2s, void* k_s2v,
  * HB_ERR_STATE without a curve, or v2v_dense == 0 before hb_build. */
 hb_status hb_apply_inclusion(hb_handle h, const void* s, void* u, int nrhs, int v2v_dense, void* stream);
 
+/* Table builder for media without closed-form ingredients (Sec. 2.3 and
+ * Sec. 4.1): the tables hb_create takes, computed on the device.
+ *
+ * hb_sweep_taylor: the near-source Taylor numbers of ns source points from
+ * the series of n^2 about each (Sec. 2.2, d = 2: Eq. recursiveT, Eq.
+ * recursiveB, Eq. C0, Eq. C1, Eq. recursiveC).  s2: HOST ns x 15, row k =
+ * S_0..S_4 of n(r_k + (X, Z))^2 = sum_j S_j(X, Z), piece j = j + 1
+ * coefficients of X^(j-m) Z^m, m = 0..j; S_0 = n(r_k)^2 > 0.  taylor: HOST
+ * ns x 46 out, row k = T_2..T_6, B_0..B_4, C_0..C_2 (the pieces of the
+ * expansions Eq. expansionT, Eq. expansionV0, Eq. expansionV1 in the same
+ * layout).  Errors: HB_ERR_ARG (null array, ns < 0, S_0 <= 0).
+ *
+ * hb_sweep_tables: per source node, the factored eikonal (Eq. faceik) on
+ * the mesh x_i = lo + i h, z_j = lo + j h (i, j < M) and the transports of
+ * v0 and v1 (Eq. equVs) on its window [w0, w1]^2 (region of interest
+ * [roi0, roi1]^2 in window indices) by Lax-Friedrichs WENO5 Gauss-Seidel
+ * sweeping (four orderings per iteration, until the largest update over the
+ * window - resp. the region of interest - is below tol, at most max_iter
+ * iterations), the points within 5 h (eikonal), 3 h (v0) and 1 h (v1) of
+ * the source fixed at their Taylor values, then 4 x 4 local cubic
+ * interpolation to the NI observation points.  n_mesh: HOST M x M, n at
+ * (x_i, z_j) in [j][i].  px, pz: HOST NI point coordinates (the tensor
+ * Chebyshev nodes of hb_tables, x fastest).  src: HOST ns node indices of
+ * the sources, taylor: HOST ns x 46 (hb_sweep_taylor).  Out (HOST, NI x ns
+ * row-major, [observation][source]): tau2, v0, v1 - the tables' columns
+ * src[k] (at a source's own node tau2 is 0, v0 = B_0 and v1 = C_0 by
+ * Eq. expansionT..V1: set those entries, which the interpolation only
+ * approximates); info: HOST ns x 6, the iterations and the last largest
+ * update of the three solves.  One CTA per source; each anti-diagonal of a
+ * sweep is updated in parallel, which gives the row-by-row Gauss-Seidel
+ * iterates bit for bit.  Device memory: ns x (5 M^2 + 7 (w1 - w0 + 1)^2) x
+ * 8 bytes.  Synchronous.  Errors: HB_ERR_ARG (null array, bad mesh - M < 8,
+ * h <= 0, window outside the mesh or under 8 points, region of interest
+ * outside the window - node index out of range, S_0 <= 0), HB_ERR_OOM,
+ * HB_ERR_CUDA. */
+hb_status hb_sweep_taylor(int ns, const double* s2, double* taylor);
+hb_status hb_sweep_tables(int M, double lo, double h, int w0, int w1, int roi0, int roi1, const double* n_mesh,
+                          int NI, const double* px, const double* pz, int ns, const int* src, const double* taylor,
+                          int max_iter, double tol, double* tau2, double* v0, double* v1, double* info);
+
 /* hb_id_batch: batched column-pivoted QR interpolative decompositions
  * (Eq. ID) of `count` complex128 matrices, with the same rules as the build:
  * pivot on the largest recomputed trailing column norm (lowest index on exact

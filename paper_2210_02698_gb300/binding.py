@@ -24,7 +24,7 @@ STATUS = {0: "HB_OK", 1: "HB_ERR_ARG", 2: "HB_ERR_CUDA", 3: "HB_ERR_OOM", 4: "HB
 EXPORTS = ["hb_create", "hb_build", "hb_set_omega", "hb_save", "hb_load", "hb_apply", "hb_apply_adjoint", "hb_set_precision",
            "hb_set_wait_selftest", "hb_device_alloc_cap",
            "hb_apply_dense", "hb_apply_dense_adjoint", "hb_entries", "hb_curve_set", "hb_curve_operators",
-           "hb_apply_inclusion", "hb_id_batch", "hb_id_batch_noalloc",
+           "hb_apply_inclusion", "hb_sweep_taylor", "hb_sweep_tables", "hb_id_batch", "hb_id_batch_noalloc",
            "hb_record_id_blocks", "hb_recorded_id_count", "hb_recorded_id_block", "hb_launch_shape", "hb_fp64_fma_peak",
            "hb_shard_rows", "hb_apply_shard", "hb_apply_shard_adjoint", "hb_host_shard_rows",
            "hb_tree_perm", "hb_proxy_rows", "hb_host_cluster_tree", "hb_host_proxy_rows", "hb_host_segment_tree", "hb_host_point_proxy_rows", "hb_info", "hb_rank_profile", "hb_set_kernel_timing",
@@ -70,6 +70,8 @@ def lib():
         L.hb_create.argtypes = [C.POINTER(Grid), C.POINTER(Tables), d, C.POINTER(Options), C.POINTER(vp)]
         L.hb_build.argtypes = [vp]
         L.hb_set_omega.argtypes = [vp, d]
+        L.hb_sweep_taylor.argtypes = [i, vp, vp]
+        L.hb_sweep_tables.argtypes = [i, d, d, i, i, i, i, vp, i, vp, vp, i, vp, vp, i, d, vp, vp, vp, vp]
         for f in ("hb_apply", "hb_apply_adjoint", "hb_apply_dense", "hb_apply_dense_adjoint"):
             getattr(L, f).argtypes = [vp, vp, vp, i, vp]
         L.hb_set_precision.argtypes = [vp, i]
@@ -113,6 +115,37 @@ def lib():
                 getattr(L, f).restype = C.c_int
         _LIB = L
     return _LIB
+
+
+def sweep_taylor(s2):
+    """hb_sweep_taylor: (ns, 15) series S_0..S_4 of n^2 about each source ->
+    (ns, 46) Taylor numbers T_2..T_6, B_0..B_4, C_0..C_2."""
+    s2 = np.ascontiguousarray(s2, dtype=np.float64)
+    if s2.ndim != 2 or s2.shape[1] != 15:
+        raise ValueError("s2 must be (ns, 15)")
+    out = np.empty((s2.shape[0], 46))
+    _check(lib().hb_sweep_taylor(s2.shape[0], s2.ctypes.data, out.ctypes.data))
+    return out
+
+
+def sweep_tables(M, lo, h, w0, w1, roi0, roi1, n_mesh, px, pz, src, taylor, max_iter=400, tol=1e-12):
+    """hb_sweep_tables: the tables' columns src of tau^2, v0, v1 (each
+    (NI, ns)) and the solves' info (ns, 6), computed on the device."""
+    n_mesh = np.ascontiguousarray(n_mesh, dtype=np.float64)
+    px = np.ascontiguousarray(px, dtype=np.float64)
+    pz = np.ascontiguousarray(pz, dtype=np.float64)
+    src = np.ascontiguousarray(src, dtype=np.int32)
+    taylor = np.ascontiguousarray(taylor, dtype=np.float64)
+    NI, ns = px.size, src.size
+    if n_mesh.shape != (M, M) or pz.size != NI or taylor.shape != (ns, 46):
+        raise ValueError("n_mesh (M, M), pz like px and taylor (ns, 46) required")
+    t2, a0, a1 = (np.empty((NI, ns)) for _ in range(3))
+    info = np.empty((ns, 6))
+    _check(lib().hb_sweep_tables(int(M), float(lo), float(h), int(w0), int(w1), int(roi0), int(roi1),
+                                 n_mesh.ctypes.data, NI, px.ctypes.data, pz.ctypes.data, ns, src.ctypes.data,
+                                 taylor.ctypes.data, int(max_iter), float(tol), t2.ctypes.data, a0.ctypes.data,
+                                 a1.ctypes.data, info.ctypes.data))
+    return t2, a0, a1, info
 
 
 def device_alloc_cap(cap_bytes=-1):

@@ -331,6 +331,24 @@ hb_status hb_set_omega(hb_handle h, double omega) {
   });
 }
 
+hb_status hb_sweep_taylor(int ns, const double* s2, double* taylor) {
+  return guarded(nullptr, [&] {
+    if (ns < 0) throw hb::arg_error("ns must be >= 0");
+    if (ns > 0 && (!s2 || !taylor)) throw hb::arg_error("null argument");
+    for (int k = 0; k < ns; ++k) hb::sweep_taylor_one(s2 + (size_t)k * 15, taylor + (size_t)k * 46);
+  });
+}
+
+hb_status hb_sweep_tables(int M, double lo, double h, int w0, int w1, int roi0, int roi1, const double* n_mesh,
+                          int NI, const double* px, const double* pz, int ns, const int* src, const double* taylor,
+                          int max_iter, double tol, double* tau2, double* v0, double* v1, double* info) {
+  return guarded(nullptr, [&] {
+    hb::NvtxRange nr("hb_sweep_tables");
+    hb::sweep_tables(M, lo, h, w0, w1, roi0, roi1, n_mesh, NI, px, pz, ns, src, taylor, max_iter, tol, tau2, v0, v1,
+                     info);
+  });
+}
+
 hb_status hb_record_id_blocks(hb_handle h, int per_level) {
   return guarded(h, [&] {
     if (!h) throw hb::arg_error("null handle");

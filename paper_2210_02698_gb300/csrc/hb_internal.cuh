@@ -333,6 +333,11 @@ namespace hb {
 hb::EntryParams entry_params(const hb_ctx* c, int transposed);
 void setup_tables(hb_ctx* c);                 // entries.cu
 void compute_self(hb_ctx* c);                 // entries.cu
+// sweep.cu: the table builder (arguments as hb_sweep_tables / hb_sweep_taylor)
+void sweep_tables(int M, double lo, double h, int w0, int w1, int roi0, int roi1, const double* n_mesh, int NI,
+                  const double* px, const double* pz, int ns, const int* src, const double* taylor, int max_iter,
+                  double tol, double* tau2, double* v0, double* v1, double* info);
+void sweep_taylor_one(const double* s2, double* out);
 void dense_apply(hb_ctx* c, const double2* s, double2* u, int nrhs, int adjoint, cudaStream_t st);
 void eval_entries(hb_ctx* c, const long long* rows, int m, const long long* cols, int n,
                   double2* out, cudaStream_t st);
