@@ -602,6 +602,86 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_inclusion(args):
+    """The inclusion apply (Sec. 3.2, Eq. m_v2v_inclu) on the workload's
+    grid with a circle of args.inclusion segments (centre (0.5, 0.5), radius
+    0.3): K^{v2v} compressed (split-BF16), the surface part in FP64 - first
+    with the dense K^{v2s} / K^{s2v}, then with their butterflies
+    (hb_curve_compress).  One JSON line; the roofline is the FP64 arithmetic
+    of the two surface butterflies (8 flops per stored complex entry and
+    right-hand side) against the measured FP64 FMA rate."""
+    import torch
+    from paper_2210_02698_gb300 import binding, build
+    build.build()
+    torch.cuda.set_device(0)
+    w = W.WORKLOADS[args.workload]
+    tab = load_tables(w)
+    op = binding.Operator(w.N, tab["nodes"], tab["tau2"], tab["v0"], tab["v1"], w.n_cells(), w.omega,
+                          eps=w.eps, leaf=w.leaf, chi=w.chi, precision=binding.HB_MIXED_BF16X3, autotune=1)
+    op.build()
+    ns = int(args.inclusion)
+    cen, lw = W.circle_segments((0.5, 0.5), 0.3, ns)
+    t0 = time.perf_counter()
+    op.set_curve(cen, lw, w.medium.n(cen[:, 0], cen[:, 1]))
+    set_s = time.perf_counter() - t0
+    R, Nv = w.nrhs, w.grid.Nv
+    s_dev = torch.from_numpy(np.ascontiguousarray(W.workload_sources(w).T)).to("cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed():
+        u = torch.empty_like(s_dev)
+        for _ in range(args.warmup):
+            op.apply_inclusion(s_dev, u, R, stream=stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            op.apply_inclusion(s_dev, u, R, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps, u
+
+    ms_dense, u_dense = timed()
+    t0 = time.perf_counter()
+    op.curve_compress(16)
+    compress_s = time.perf_counter() - t0
+    ms_bf, u_bf = timed()
+    info = [op.curve_info(q) for q in (0, 1)]
+    entries = sum(e for _, _, e in info)
+    # the surface butterflies alone: the difference to the volume apply
+    u = torch.empty_like(s_dev)
+    for _ in range(args.warmup):
+        op.apply(s_dev, u, R, stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        op.apply(s_dev, u, R, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_v2v = e0.elapsed_time(e1) / args.steps
+    peak = binding.fp64_fma_peak(stream)
+    surface_ms = max(ms_bf - ms_v2v, 1e-9)
+    achieved = 8.0 * entries * R / (surface_ms * 1e-3) / 1e12
+    rel = float(torch.linalg.norm(u_bf - u_dense) / torch.linalg.norm(u_dense))
+    print(json.dumps({
+        "metric": "inclusion apply N_v*RHS/s (K^{v2v} compressed, surface part FP64)", "unit": UNIT,
+        "value": Nv * R / (ms_bf * 1e-3), "ms_per_step": ms_bf, "higher_is_better": True,
+        "steps": args.steps, "warmup": args.warmup, "data": "synthetic",
+        "config": {"workload": describe(w), "segments": ns, "curve": "circle centre (0.5, 0.5) radius 0.3"},
+        "dense_surface": {"value": Nv * R / (ms_dense * 1e-3), "ms_per_step": ms_dense,
+                          "bytes": 2 * ns * Nv * 16},
+        "volume_only_ms": ms_v2v,
+        "butterflies": {"v2s": {"levels": info[0][0], "max_rank": info[0][1], "entries": info[0][2]},
+                        "s2v": {"levels": info[1][0], "max_rank": info[1][1], "entries": info[1][2]},
+                        "compress_s": compress_s, "curve_set_s": set_s},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "kernel": "surface butterflies (inclusion apply minus the volume apply)",
+                     "peak_kind": "measured FP64 FMA loop"},
+        "rel_l2_compressed_vs_dense_surface": rel}), flush=True)
+    op.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -616,6 +696,9 @@ def main():
                          "launch, one launch per dependency depth, that with the leaf outputs on the "
                          "tcgen05 tensor-core kernel, the cone launch, fused level pairs, or every depth "
                          "in one cooperative launch with grid barriers")
+    ap.add_argument("--inclusion", type=int, default=0, metavar="NS",
+                    help="time the inclusion apply with a circle of NS segments instead (dense and compressed "
+                         "surface operators)")
     ap.add_argument("--one-core-sample", nargs=3, metavar=("WORKLOAD", "ROWS", "SEED"), help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.one_core_sample:
@@ -624,6 +707,8 @@ def main():
         w = W.WORKLOADS[name]
         _, _, dt = cpu_oracle_sample(w, load_tables(w), int(rows_n), seed=int(seed))
         print(dt, flush=True)
+    elif args.inclusion:
+        run_inclusion(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

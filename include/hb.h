@@ -176,7 +176,7 @@ hb_status hb_build(hb_handle h);
  * omega-dependent self terms; frees the factors, plans and apply scratch of
  * a previous hb_build (the handle is then unbuilt: call hb_build again
  * before hb_apply) and assembles a curve set with hb_curve_set again at the
- * new frequency.  The result equals a handle created at omega with the same
+ * new frequency (its compressed operators of hb_curve_compress are dropped).  The result equals a handle created at omega with the same
  * tables.  Synchronous.  Errors: HB_ERR_ARG (null handle, omega <= 0 or not
  * finite), HB_ERR_OOM, HB_ERR_CUDA. */
 hb_status hb_set_omega(hb_handle h, double omega);
@@ -303,9 +303,10 @@ hb_status hb_entries(hb_handle h, const long long* rows, int m, const long long*
  * The total field vanishes on the curve (Eq. sie; Eq. m_sie: K^{s2s} P = U^inc).
  *
  * hb_curve_set: evaluates the three operators densely on the device and
- * factors K^{s2s} (LU with partial pivoting); replaces an earlier curve.
- * Synchronous.  Device memory: (2 ns N_v + ns^2) x 16 bytes plus ns x nrhs x
- * 16 bytes at the first hb_apply_inclusion, owned by the handle until the
+ * factors K^{s2s} (LU with partial pivoting) and keeps its inverse (N_s^2
+ * more complex values); replaces an earlier curve.
+ * Synchronous.  Device memory: (2 ns N_v + 2 ns^2) x 16 bytes plus 2 ns x
+ * nrhs x 16 bytes at the first hb_apply_inclusion, owned by the handle until the
  * next hb_curve_set or hb_destroy.  Errors: HB_ERR_ARG for ns outside
  * [1, 16384], a non-finite centre, a length or n that is not positive, or a
  * singular K^{s2s} (the handle then has no curve); HB_ERR_OOM. */
@@ -327,6 +328,23 @@ hb_status hb_curve_operators(hb_handle h, void* k_s2s, void* k_v2s, void* k_s2v,
  * surface vectors: make it outside a CUDA graph capture.  Errors:
  * HB_ERR_STATE without a curve, or v2v_dense == 0 before hb_build. */
 hb_status hb_apply_inclusion(hb_handle h, const void* s, void* u, int nrhs, int v2v_dense, void* stream);
+
+/* hb_curve_compress: K^{v2s} and K^{s2v} of the curve set with hb_curve_set
+ * as butterflies (Sec. 4.2, the K^{v2s} / K^{s2v} items; Sec. 4.2.1): one
+ * each between the cells' cluster tree and a K-D tree over the segment
+ * centres with leaves of at most leaf_s segments, both cut at L = min(L_v,
+ * L_s) levels; proxy rows by Eq. proxyv2v with the other set's points as
+ * seeds (the handle's chi and nbr_radius_h), IDs at the handle's eps.  The
+ * dense K^{v2s} / K^{s2v} are freed; hb_apply_inclusion then applies the
+ * butterflies (FP64) around the inverse of K^{s2s}.  A later hb_curve_set
+ * or hb_set_omega drops them.  Synchronous.  Errors: HB_ERR_STATE without
+ * a curve, HB_ERR_ARG (leaf_s < 1), HB_ERR_UNSUPPORTED (an empty tree node),
+ * HB_ERR_OOM, HB_ERR_CUDA.
+ * hb_curve_info: of the compressed K^{v2s} (which = 0) or K^{s2v} (1): its
+ * levels L, largest rank and stored complex entries.  HB_ERR_STATE before
+ * hb_curve_compress. */
+hb_status hb_curve_compress(hb_handle h, int leaf_s);
+hb_status hb_curve_info(hb_handle h, int which, int* levels, int* max_rank, long long* entries);
 
 /* Table builder for media without closed-form ingredients (Sec. 2.3 and
  * Sec. 4.1): the tables hb_create takes, computed on the device.

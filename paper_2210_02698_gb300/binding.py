@@ -24,7 +24,7 @@ STATUS = {0: "HB_OK", 1: "HB_ERR_ARG", 2: "HB_ERR_CUDA", 3: "HB_ERR_OOM", 4: "HB
 EXPORTS = ["hb_create", "hb_build", "hb_set_omega", "hb_save", "hb_load", "hb_apply", "hb_apply_adjoint", "hb_set_precision",
            "hb_set_wait_selftest", "hb_device_alloc_cap",
            "hb_apply_dense", "hb_apply_dense_adjoint", "hb_entries", "hb_curve_set", "hb_curve_operators",
-           "hb_apply_inclusion", "hb_sweep_taylor", "hb_sweep_tables", "hb_id_batch", "hb_id_batch_noalloc",
+           "hb_apply_inclusion", "hb_curve_compress", "hb_curve_info", "hb_sweep_taylor", "hb_sweep_tables", "hb_id_batch", "hb_id_batch_noalloc",
            "hb_record_id_blocks", "hb_recorded_id_count", "hb_recorded_id_block", "hb_launch_shape", "hb_fp64_fma_peak",
            "hb_shard_rows", "hb_apply_shard", "hb_apply_shard_adjoint", "hb_host_shard_rows",
            "hb_tree_perm", "hb_proxy_rows", "hb_host_cluster_tree", "hb_host_proxy_rows", "hb_host_segment_tree", "hb_host_point_proxy_rows", "hb_info", "hb_rank_profile", "hb_set_kernel_timing",
@@ -71,6 +71,8 @@ def lib():
         L.hb_build.argtypes = [vp]
         L.hb_set_omega.argtypes = [vp, d]
         L.hb_sweep_taylor.argtypes = [i, vp, vp]
+        L.hb_curve_compress.argtypes = [vp, i]
+        L.hb_curve_info.argtypes = [vp, i, C.POINTER(i), C.POINTER(i), C.POINTER(ll)]
         L.hb_sweep_tables.argtypes = [i, d, d, i, i, i, i, vp, i, vp, vp, i, vp, vp, i, d, vp, vp, vp, vp]
         for f in ("hb_apply", "hb_apply_adjoint", "hb_apply_dense", "hb_apply_dense_adjoint"):
             getattr(L, f).argtypes = [vp, vp, vp, i, vp]
@@ -315,6 +317,17 @@ class Operator:
         p = (lambda t, n, name: None if t is None else _device_buf(t, n, name))
         self._call("hb_curve_operators", p(k_s2s, ns * ns, "k_s2s"), p(k_v2s, ns * self.Nv, "k_v2s"),
                    p(k_s2v, ns * self.Nv, "k_s2v"), _stream_ptr(stream))
+
+    def curve_compress(self, leaf_s=16):
+        """hb_curve_compress: K^{v2s} and K^{s2v} of the curve as butterflies."""
+        self._call("hb_curve_compress", int(leaf_s))
+
+    def curve_info(self, which):
+        """hb_curve_info: (levels, max_rank, entries) of the compressed K^{v2s}
+        (which = 0) or K^{s2v} (1)."""
+        lv, mr, en = C.c_int(), C.c_int(), C.c_longlong()
+        self._call("hb_curve_info", int(which), C.byref(lv), C.byref(mr), C.byref(en))
+        return lv.value, mr.value, en.value
 
     def apply_inclusion(self, s, u, nrhs, v2v_dense=False, stream=None):
         """hb_apply_inclusion: u = (K^{v2v} + K^{s2v} (K^{s2s})^{-1} K^{v2s}) h^2 s."""

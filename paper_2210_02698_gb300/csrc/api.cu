@@ -331,6 +331,22 @@ hb_status hb_set_omega(hb_handle h, double omega) {
   });
 }
 
+hb_status hb_curve_compress(hb_handle h, int leaf_s) {
+  return guarded(h, [&] {
+    if (!h) throw hb::arg_error("null handle");
+    hb::NvtxRange nr("hb_curve_compress");
+    hb::curve_compress(h, leaf_s);
+  });
+}
+
+hb_status hb_curve_info(hb_handle h, int which, int* levels, int* max_rank, long long* entries) {
+  return guarded(h, [&] {
+    if (!h || !levels || !max_rank || !entries) throw hb::arg_error("null argument");
+    if (which != 0 && which != 1) throw hb::arg_error("which must be 0 (K^{v2s}) or 1 (K^{s2v})");
+    hb::curve_bf_info(h, which, levels, max_rank, entries);
+  });
+}
+
 hb_status hb_sweep_taylor(int ns, const double* s2, double* taylor) {
   return guarded(nullptr, [&] {
     if (ns < 0) throw hb::arg_error("ns must be >= 0");

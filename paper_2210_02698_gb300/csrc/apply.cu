@@ -208,6 +208,19 @@ void ensure_scratch(hb_ctx* c, int nrhs, bool fp64) {
   if (fresh) HB_CUDA(cudaDeviceSynchronize());
 }
 
+}  // namespace
+
+// One launch of FP64 step tasks (one CTA each), for other operators'
+// butterflies (curve_bf.cu).
+void run_tasks_fp64(const Task* d_tasks, int n, const double2* F, double2* x, double2* y, double2* xh, int R,
+                    cudaStream_t st) {
+  if (n <= 0) return;
+  step_kernel<double2><<<n, 128, 0, st>>>(d_tasks, F, x, y, xh, R);
+  HB_CHECK_LAUNCH();
+}
+
+namespace {
+
 template <class C>
 void run_steps(hb_ctx* c, const C* F, int nrhs, int dir, cudaStream_t st, TimerScope& ts) {
   const std::vector<int>& sb = c->step_begin[dir];

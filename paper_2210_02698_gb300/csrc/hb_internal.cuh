@@ -310,10 +310,12 @@ struct hb_ctx {
   double2* d_cellpts = nullptr;    // N_v cell centres (x, z)
   double2* d_lu = nullptr;         // K^{s2s} LU-factored in place (ns x ns, column-major)
   int* d_piv = nullptr;            // its row interchanges
+  double2* d_inv = nullptr;        // (K^{s2s})^{-1} from the LU factors, ns x ns column-major
   double2* d_kv2s = nullptr;       // K^{v2s}, ns x N_v column-major
   double2* d_ks2v = nullptr;       // K^{s2v}, N_v x ns column-major
-  double2* d_cy = nullptr;         // surface vectors of an apply, ns x cy_cap
+  double2* d_cy = nullptr;         // surface vectors of an apply, 2 ns x cy_cap (Y, then P)
   int cy_cap = 0;
+  void* curve_bf[2] = {nullptr, nullptr};   // hb_curve_compress: K^{v2s} (0), K^{s2v} (1) as butterflies
 
   // hb_record_id_blocks: blocks per butterfly level to keep, and the kept ones
   int id_rec_per_level = 0;
@@ -391,6 +393,26 @@ void flow_launch_shard(void* plan, const uint4* F, const double2* s, double scal
                        int* err, long long budget, cudaStream_t st);
 // inclusion.cu
 void curve_set(hb_ctx* c, const double* centers, const double* lengths, const double* n_seg, long long ns);
+// One column of a sampled curve-operator block: rows' points obs[obs0,
+// obs0 + m) against the source point src, times w, into out[out_off ..].
+struct GreenCol {
+  long long obs0;
+  long long out_off;
+  double2 src;
+  double w;
+  int m;
+  int pad;
+};
+void green_jobs(const hb_ctx* c, const double2* d_obs, const GreenCol* d_jobs, long long njobs, double2* d_out,
+                cudaStream_t st);   // inclusion.cu
+// curve_bf.cu: K^{v2s} and K^{s2v} of the curve as butterflies
+void curve_compress(hb_ctx* c, int leaf_s);
+void curve_bf_free(hb_ctx* c);
+void curve_bf_info(const hb_ctx* c, int which, int* levels, int* max_rank, long long* entries);
+void curve_bf_apply(hb_ctx* c, int which, const double2* x_nat, long long ldx, double scale, double2* y_nat,
+                    long long ldy, int accumulate, int nrhs, cudaStream_t st);
+void run_tasks_fp64(const Task* d_tasks, int n, const double2* F, double2* x, double2* y, double2* xh, int R,
+                    cudaStream_t st);   // apply.cu
 void curve_free(hb_ctx* c);
 void curve_operators(hb_ctx* c, double2* k_s2s, double2* k_v2s, double2* k_s2v, cudaStream_t st);
 void apply_inclusion(hb_ctx* c, const double2* s, double2* u, int nrhs, int v2v_dense, cudaStream_t st);

@@ -14,10 +14,11 @@
 // and g = v0 f0 + v1 f1 (Eq. babich) with tau^2, v0, v1 interpolated at the
 // points from the tables (Eq. chebinterp), as for K^{v2v}.
 //
-// This is the dense form: K^{v2s} and K^{s2v} are stored (2 N_s N_v complex
-// values), K^{s2s} is factored by LU with partial pivoting once per curve,
-// and an apply is two dense products and two triangular solves on top of
-// the K^{v2v} apply (dense or compressed).  FP64 throughout.
+// K^{v2s} and K^{s2v} are stored dense (2 N_s N_v complex values) or, after
+// hb_curve_compress, as butterflies (curve_bf.cu); K^{s2s} is factored by
+// LU with partial pivoting once per curve and inverted from the factors, so
+// an apply is three products (dense, or butterfly - dense - butterfly) on
+// top of the K^{v2v} apply (dense or compressed).  FP64 throughout.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -131,6 +132,62 @@ __global__ void __launch_bounds__(256) green_columns_kernel(PointTables P, const
       val = make_double2(sgn * wb * g.x, sgn * wb * g.y);
     }
     out[(size_t)b * ldo + a] = val;
+  }
+}
+
+// Batched columns of curve-operator blocks: job q (one CTA) writes
+// out[J.out_off + a] = J.w g(obs[J.obs0 + a], J.src) for a < J.m - the
+// same evaluation as green_columns_kernel, for sampled blocks whose rows
+// are gathered into obs.
+__global__ void __launch_bounds__(256) green_jobs_kernel(PointTables P, const double2* __restrict__ obs,
+                                                         const GreenCol* __restrict__ jobs,
+                                                         double2* __restrict__ out) {
+  __shared__ double G[3 * CMAX_NI * CMAX_NI];
+  __shared__ double bw[2][CMAX_NI];
+  __shared__ double Ls[2][CMAX_NI];
+  const int nI = P.nI, NI = P.NI, t = threadIdx.x;
+  const GreenCol J = jobs[blockIdx.x];
+  if (t < 2 * nI) {
+    const int d = t / nI, k = t % nI;
+    const double* nd = P.nodes + d * nI;
+    double p = 1.0;
+    for (int q = 0; q < nI; ++q)
+      if (q != k) p *= (nd[k] - nd[q]);
+    bw[d][k] = 1.0 / p;
+  }
+  __syncthreads();
+  if (t < 2) basis_at(P.nodes + t * nI, bw[t], nI, t == 0 ? J.src.x : J.src.y, Ls[t]);
+  __syncthreads();
+  for (int idx = t; idx < 3 * NI; idx += blockDim.x) {
+    const int q = idx / NI, i = idx % NI;
+    const double* Fr = P.tab + ((size_t)q * NI + i) * NI;
+    double acc = 0.0;
+    for (int j2 = 0; j2 < nI; ++j2) {
+      double a2 = 0.0;
+      for (int j1 = 0; j1 < nI; ++j1) a2 = fma(Fr[j2 * nI + j1], Ls[0][j1], a2);
+      acc = fma(Ls[1][j2], a2, acc);
+    }
+    G[idx] = acc;
+  }
+  __syncthreads();
+  for (int a = t; a < J.m; a += blockDim.x) {
+    const double2 o = obs[J.obs0 + a];
+    double Lx[CMAX_NI], Lz[CMAX_NI];
+    basis_at(P.nodes, bw[0], nI, o.x, Lx);
+    basis_at(P.nodes + nI, bw[1], nI, o.y, Lz);
+    double f[3];
+    for (int q = 0; q < 3; ++q) {
+      const double* Gq = G + q * NI;
+      double acc = 0.0;
+      for (int i2 = 0; i2 < nI; ++i2) {
+        double a2 = 0.0;
+        for (int i1 = 0; i1 < nI; ++i1) a2 = fma(Lx[i1], Gq[i2 * nI + i1], a2);
+        acc = fma(Lz[i2], a2, acc);
+      }
+      f[q] = acc;
+    }
+    const double2 g = hb_green(f[0], f[1], f[2], P.omega);
+    out[J.out_off + a] = make_double2(J.w * g.x, J.w * g.y);
   }
 }
 
@@ -266,6 +323,13 @@ __global__ void __launch_bounds__(256) lu_solve_kernel(const double2* __restrict
   }
 }
 
+// A = the n x n identity (column-major)
+__global__ void identity_kernel(double2* __restrict__ A, long long n) {
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n * n;
+       idx += (long long)gridDim.x * blockDim.x)
+    A[idx] = make_double2(idx % n == idx / n ? 1.0 : 0.0, 0.0);
+}
+
 // Y[:, r] (= or +=) alpha A X[:, r] for r < R; A column-major m x k, X with
 // leading dimension ldx, Y with ldy.  One thread per output (row fastest).
 __global__ void cgemm_kernel(const double2* __restrict__ A, long long m, long long k, const double2* __restrict__ X,
@@ -325,16 +389,28 @@ void assemble(const hb_ctx* c, const double2* seg, const double* w, const double
 
 }  // namespace
 
+void green_jobs(const hb_ctx* c, const double2* d_obs, const GreenCol* d_jobs, long long njobs, double2* d_out,
+                cudaStream_t st) {
+  const PointTables P = point_tables(c);
+  for (long long b0 = 0; b0 < njobs; b0 += (1LL << 30)) {
+    const unsigned n = (unsigned)std::min<long long>(njobs - b0, 1LL << 30);
+    green_jobs_kernel<<<n, 256, 0, st>>>(P, d_obs, d_jobs + b0, d_out);
+    HB_CHECK_LAUNCH();
+  }
+}
+
 void curve_free(hb_ctx* c) {
   for (void* p : {(void*)c->d_seg, (void*)c->d_segw, (void*)c->d_segn, (void*)c->d_cellpts, (void*)c->d_lu,
-                  (void*)c->d_piv, (void*)c->d_kv2s, (void*)c->d_ks2v, (void*)c->d_cy})
+                  (void*)c->d_piv, (void*)c->d_kv2s, (void*)c->d_ks2v, (void*)c->d_cy, (void*)c->d_inv})
     dev_free(p);
+  c->d_inv = nullptr;
   c->d_seg = nullptr;
   c->d_segw = c->d_segn = nullptr;
   c->d_cellpts = c->d_lu = c->d_kv2s = c->d_ks2v = c->d_cy = nullptr;
   c->d_piv = nullptr;
   c->ns = 0;
   c->cy_cap = 0;
+  curve_bf_free(c);
 }
 
 void curve_set(hb_ctx* c, const double* centers, const double* lengths, const double* n_seg, long long ns) {
@@ -379,6 +455,14 @@ void curve_set(hb_ctx* c, const double* centers, const double* lengths, const do
       int sing = 0;
       HB_CUDA(cudaMemcpy(&sing, d_sing, sizeof(int), cudaMemcpyDeviceToHost));
       if (sing) throw Error{HB_ERR_ARG, "K^{s2s} is singular: a zero pivot in its LU factorisation"};
+      // the inverse, column by column from the factors (an apply is then one
+      // product instead of two sequential triangular solves per column)
+      c->d_inv = dev_alloc<double2>((size_t)ns * ns);
+      identity_kernel<<<(unsigned)std::min<long long>((ns * ns + 255) / 256, 152LL * 8), 256>>>(c->d_inv, ns);
+      HB_CHECK_LAUNCH();
+      lu_solve_kernel<<<(unsigned)ns, 256>>>(c->d_lu, c->d_piv, n, c->d_inv, ns);
+      HB_CHECK_LAUNCH();
+      HB_CUDA(cudaDeviceSynchronize());
     } catch (...) {
       cudaDeviceSynchronize();
       dev_free(d_sing);
@@ -405,7 +489,7 @@ void apply_inclusion(hb_ctx* c, const double2* s, double2* u, int nrhs, int v2v_
     dev_free(c->d_cy);
     c->d_cy = nullptr;
     c->cy_cap = 0;
-    c->d_cy = dev_alloc<double2>((size_t)c->ns * nrhs);
+    c->d_cy = dev_alloc<double2>((size_t)c->ns * nrhs * 2);
     c->cy_cap = nrhs;
     HB_CUDA(cudaDeviceSynchronize());
   }
@@ -414,15 +498,25 @@ void apply_inclusion(hb_ctx* c, const double2* s, double2* u, int nrhs, int v2v_
   else apply_bf(c, s, u, nrhs, 0, c->opt.precision, st);
   const long long ns = c->ns;
   auto grid = [](long long total) { return (unsigned)std::max<long long>(1, std::min<long long>((total + 255) / 256, 152LL * 8)); };
+  const bool compressed = c->curve_bf[0] && c->curve_bf[1];
   // Y = K^{v2s} I = h^2 K^{v2s} s
-  cgemm_kernel<<<grid(ns * nrhs), 256, 0, st>>>(c->d_kv2s, ns, c->Nv, s, c->Nv, c->d_cy, ns, nrhs, c->h * c->h, 0);
-  HB_CHECK_LAUNCH();
+  if (compressed) {
+    curve_bf_apply(c, 0, s, c->Nv, c->h * c->h, c->d_cy, ns, 0, nrhs, st);
+  } else {
+    cgemm_kernel<<<grid(ns * nrhs), 256, 0, st>>>(c->d_kv2s, ns, c->Nv, s, c->Nv, c->d_cy, ns, nrhs, c->h * c->h, 0);
+    HB_CHECK_LAUNCH();
+  }
   // P = (K^{s2s})^{-1} Y
-  lu_solve_kernel<<<(unsigned)nrhs, 256, 0, st>>>(c->d_lu, c->d_piv, (int)ns, c->d_cy, ns);
+  double2* P = c->d_cy + (size_t)ns * nrhs;
+  cgemm_kernel<<<grid(ns * nrhs), 256, 0, st>>>(c->d_inv, ns, ns, c->d_cy, ns, P, ns, nrhs, 1.0, 0);
   HB_CHECK_LAUNCH();
   // U += K^{s2v} P
-  cgemm_kernel<<<grid(c->Nv * nrhs), 256, 0, st>>>(c->d_ks2v, c->Nv, ns, c->d_cy, ns, u, c->Nv, nrhs, 1.0, 1);
-  HB_CHECK_LAUNCH();
+  if (compressed) {
+    curve_bf_apply(c, 1, P, ns, 1.0, u, c->Nv, 1, nrhs, st);
+  } else {
+    cgemm_kernel<<<grid(c->Nv * nrhs), 256, 0, st>>>(c->d_ks2v, c->Nv, ns, P, ns, u, c->Nv, nrhs, 1.0, 1);
+    HB_CHECK_LAUNCH();
+  }
 }
 
 }  // namespace hb
