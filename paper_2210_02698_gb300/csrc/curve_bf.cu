@@ -109,6 +109,21 @@ __global__ void scatter_tree_kernel(const double2* __restrict__ y, const long lo
   }
 }
 
+// One copy per CTA: rows [row0, row0 + rows) of the column-major block at
+// src + src_off (ld src_ld, cols columns) to a rows x cols block at dst_off.
+struct RowChunk {
+  long long src_off, dst_off;
+  int src_ld, rows, cols, row0;
+};
+__global__ void rechunk_kernel(const double2* __restrict__ src, const RowChunk* __restrict__ ch,
+                               double2* __restrict__ dst) {
+  const RowChunk c = ch[blockIdx.x];
+  for (long long e = threadIdx.x; e < (long long)c.rows * c.cols; e += blockDim.x) {
+    const long long col = e / c.rows, r = e % c.rows;
+    dst[c.dst_off + e] = src[c.src_off + col * c.src_ld + c.row0 + r];
+  }
+}
+
 unsigned grid_for(long long total) {
   return (unsigned)std::max<long long>(1, std::min<long long>((total + 255) / 256, 152LL * 8));
 }
@@ -316,13 +331,54 @@ CurveBfly* build_bfly(const hb_ctx* c, const BfSide& R, const BfSide& C, int L) 
     parts.push_back({KL.take(), kacc});
     fbase += kacc;
     // the factor arena, in task order
-    B->d_F = dev_alloc<double2>((size_t)std::max<long long>(fbase, 1));
+    DevBuf<double2> F;
+    F.p = dev_alloc<double2>((size_t)std::max<long long>(fbase, 1));
     long long at = 0;
     for (auto& q : parts) {
-      if (q.second) HB_CUDA(cudaMemcpy(B->d_F + at, q.first, sizeof(double2) * q.second, cudaMemcpyDeviceToDevice));
+      if (q.second) HB_CUDA(cudaMemcpy(F.p + at, q.first, sizeof(double2) * q.second, cudaMemcpyDeviceToDevice));
       at += q.second;
     }
     free_parts();
+    // tasks of more than CHUNK output rows split by rows (more CTAs per
+    // step: a level has only 2^L tasks), each chunk's factor rows copied to
+    // a block of their own (the tasks read F with the leading dimension
+    // r_out)
+    constexpr int CHUNK = 64;
+    std::vector<Task> split;
+    std::vector<RowChunk> chunks;
+    std::vector<int> sb2{0};
+    long long nf = 0;
+    for (size_t st = 0; st + 1 < sb.size(); ++st) {
+      for (int q = sb[st]; q < sb[st + 1]; ++q) {
+        const Task& t = tasks[(size_t)q];
+        const int cols = t.r_in[0] + (t.nterm == 2 ? t.r_in[1] : 0);
+        for (int r0 = 0; r0 < t.r_out; r0 += CHUNK) {
+          const int cr = std::min(CHUNK, t.r_out - r0);
+          Task u = t;
+          u.y_off = t.y_off + r0;
+          u.r_out = cr;
+          u.f_off[0] = nf;
+          if (t.nterm == 2) u.f_off[1] = nf + (long long)cr * t.r_in[0];
+          split.push_back(u);
+          chunks.push_back(RowChunk{t.f_off[0], nf, t.r_out, cr, cols, r0});
+          nf += (long long)cr * cols;
+        }
+      }
+      sb2.push_back((int)split.size());
+    }
+    B->d_F = dev_alloc<double2>((size_t)std::max<long long>(nf, 1));
+    if (!chunks.empty()) {
+      DevBuf<RowChunk> d_ch;
+      to_dev(d_ch, chunks);
+      for (size_t b0 = 0; b0 < chunks.size(); b0 += (1u << 30)) {
+        const unsigned n = (unsigned)std::min<size_t>(chunks.size() - b0, 1u << 30);
+        rechunk_kernel<<<n, 256>>>(F.p, d_ch.p + b0, B->d_F);
+        HB_CHECK_LAUNCH();
+      }
+      HB_CUDA(cudaDeviceSynchronize());
+    }
+    tasks.swap(split);
+    sb.swap(sb2);
     B->entries = fbase;
     B->xh_rows = xh;
     B->step_begin = sb;
