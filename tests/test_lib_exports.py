@@ -285,10 +285,36 @@ def test_binding_methods_marshal_through_a_null_handle(L):
     calls = [lambda: op.launch_shape(False, 1), lambda: op.launch_shape(True, 2),
              lambda: op.record_id_blocks(4), lambda: op.recorded_id_blocks(), lambda: op.info(),
              lambda: op.tree_perm() if hasattr(op, "Nv") else op._call("hb_tree_perm", None),
-             lambda: op.set_kernel_timing(True), lambda: op.set_precision(binding.HB_FP64)]
+             lambda: op.set_kernel_timing(True), lambda: op.set_precision(binding.HB_FP64),
+             lambda: op.set_omega(2.0), lambda: op.curve_compress(16), lambda: op.curve_info(0)]
     for f in calls:
         with pytest.raises(binding.HBError) as e:
             f()
         assert e.value.status == binding.HB_ERR_ARG
     v = C.c_double()
     assert L.hb_fp64_fma_peak(None, None) == binding.HB_ERR_ARG
+
+
+def test_table_builder_arguments_need_no_device(L):
+    """hb_sweep_tables checks its mesh, sizes and node indices before any
+    device call, so the errors come back without a GPU."""
+    from paper_2210_02698_gb300 import binding
+    M = 16
+    n = np.ones((M, M))
+    px = pz = np.array([0.25, 0.75])
+    tin = np.zeros((1, 46))
+    tin[0, 0] = 1.0
+    src = np.array([0], dtype=np.int32)
+    for bad in ((M, 0.0, 0.1, 2, M, 0, 4), (M, 0.0, -0.1, 2, 12, 0, 4), (4, 0.0, 0.1, 0, 3, 0, 1),
+                (M, 0.0, 0.1, 2, 12, 0, 11)):
+        with pytest.raises(binding.HBError) as e:
+            binding.sweep_tables(*bad, n[:bad[0], :bad[0]], px, pz, src, tin)
+        assert e.value.status == binding.HB_ERR_ARG
+    with pytest.raises(binding.HBError) as e:
+        binding.sweep_tables(M, 0.0, 0.1, 2, 12, 0, 4, n, px, pz, np.array([2], dtype=np.int32), tin)
+    assert e.value.status == binding.HB_ERR_ARG        # node index out of range
+    bad_t = tin.copy()
+    bad_t[0, 0] = 0.0
+    with pytest.raises(binding.HBError) as e:
+        binding.sweep_tables(M, 0.0, 0.1, 2, 12, 0, 4, n, px, pz, src, bad_t)
+    assert e.value.status == binding.HB_ERR_ARG        # S0 = n0^2 must be positive
