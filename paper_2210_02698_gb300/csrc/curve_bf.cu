@@ -172,6 +172,11 @@ void id_level(const hb_ctx* c, double2* d_A, const std::vector<int>& m, const st
     sacc += n[(size_t)b];
     max_n = std::max(max_n, n[(size_t)b]);
   }
+  // the ID kernel keeps 28 bytes per column of a block in shared memory
+  if (max_n > 8000)
+    throw Error{HB_ERR_UNSUPPORTED,
+                "a curve butterfly block with more than 8000 columns (too few tree levels: more segments or a "
+                "smaller leaf_s)"};
   DevBuf<int> d_m, d_n, d_rank, d_perm;
   DevBuf<long long> d_a, d_s, d_v;
   to_dev(d_m, m);
