@@ -348,7 +348,7 @@ CurveBfly* build_bfly(const hb_ctx* c, const BfSide& R, const BfSide& C, int L) 
     // step: a level has only 2^L tasks), each chunk's factor rows copied to
     // a block of their own (the tasks read F with the leading dimension
     // r_out)
-    constexpr int CHUNK = 64;
+    constexpr int CHUNK = 16;
     std::vector<Task> split;
     std::vector<RowChunk> chunks;
     std::vector<int> sb2{0};
